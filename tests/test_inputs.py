@@ -1,0 +1,159 @@
+"""Pins of the input generators (meshes, canonical topology, BC dual basis,
+operator assembly) against what the paper and the mathematics fix."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2510_07989_gb300.inputs import meshes as MS
+from paper_2510_07989_gb300.inputs.dual import dual_basis, gram_matrix, triangle_rule
+
+
+@pytest.mark.parametrize("make,counts,chi", [
+    (lambda: MS.icosphere(1), (42, 80, 120), 2),
+    (lambda: MS.icosphere(3), (642, 1280, 1920), 2),
+    (lambda: MS.torus(1.0, 0.3, 64, 24), (1536, 3072, 4608), 0),
+    (lambda: MS.cube(2.0, 24), (3458, 6912, 10368), 2),
+    (lambda: MS.geodesic_sphere(5), (252, 500, 750), 2),
+])
+def test_mesh_counts_euler(make, counts, chi):
+    """Counts of the configured workloads; V - E + F = 2 (sphere) or 0 (torus); E = 3F/2."""
+    m = make()
+    assert (m.nv, m.nf, m.ne) == counts
+    assert m.nv - m.ne + m.nf == chi
+    assert 2 * m.ne == 3 * m.nf
+
+
+def test_canonical_edge_rule():
+    """v^- < v^+; c^+ traverses v^- -> v^+ counter-clockwise (lies left of the
+    edge seen from outside); x^+/x^- are the opposite vertices."""
+    m = MS.torus(1.0, 0.3, 12, 8)
+    assert np.all(m.ev[:, 0] < m.ev[:, 1])
+    for e in range(m.ne):
+        a, b = m.ev[e]
+        fp, fm = m.ef[e]
+        tp, tm = list(m.tris[fp]), list(m.tris[fm])
+        i = tp.index(a)
+        assert tp[(i + 1) % 3] == b and tp[(i + 2) % 3] == m.eo[e, 0]
+        j = tm.index(b)
+        assert tm[(j + 1) % 3] == a and tm[(j + 2) % 3] == m.eo[e, 1]
+    # outward orientation: signed volume > 0
+    v = m.verts[m.tris]
+    vol = np.einsum("fi,fi->f", v[:, 0], np.cross(v[:, 1], v[:, 2])).sum() / 6
+    assert vol > 0
+
+
+@pytest.mark.parametrize("make", [lambda: MS.icosphere(2), lambda: MS.torus(1.0, 0.3, 16, 8), lambda: MS.cube(2.0, 4)])
+def test_incidence_orthogonality(make):
+    """Sigma^T Lambda = 0 exactly, in integers (Section IV-B)."""
+    m = make()
+    ne = m.ne
+    L = sp.csr_matrix((np.r_[np.ones(ne), -np.ones(ne)], (np.r_[np.arange(ne), np.arange(ne)], np.r_[m.ev[:, 1], m.ev[:, 0]])),
+                      shape=(ne, m.nv), dtype=np.int64)
+    S = sp.csr_matrix((np.r_[np.ones(ne), -np.ones(ne)], (np.r_[np.arange(ne), np.arange(ne)], np.r_[m.ef[:, 0], m.ef[:, 1]])),
+                      shape=(ne, m.nf), dtype=np.int64)
+    assert (S.T @ L).count_nonzero() == 0
+
+
+def test_triangle_rules_exactness():
+    """Each rule integrates monomials up to its degree exactly on the reference
+    triangle (int x^a y^b = a! b! / (a+b+2)!)."""
+    from math import factorial
+    for n, deg in ((1, 1), (3, 2), (4, 3), (6, 4), (7, 5)):
+        bary, w = triangle_rule(n)
+        x, y = bary[:, 1], bary[:, 2]
+        for a in range(deg + 1):
+            for b in range(deg + 1 - a):
+                exact = factorial(a) * factorial(b) / factorial(a + b + 2)
+                assert abs(0.5 * np.sum(w * x ** a * y ** b) - exact) < 1e-13
+
+
+@pytest.mark.parametrize("level", [1, 2, 3])
+def test_gram_well_conditioned(level):
+    """G = <n x f_m, g_n> is sparse, has a positive diagonal and is well
+    conditioned independently of the mesh level (Section III)."""
+    m = MS.icosphere(level)
+    d = dual_basis(m)
+    r, c, v = gram_matrix(m, d)
+    G = sp.coo_matrix((v, (r, c)), shape=(m.ne, m.ne)).toarray()
+    s = np.linalg.svd(G, compute_uv=False)
+    assert np.all(np.diag(G) > 0)
+    assert s[0] / s[-1] < 4.0
+
+
+def test_bc_loops_divergence_free_and_charge():
+    """Sigma-combinations of BC functions are divergence free (BC loops) and the
+    divergence of every BC function integrates to zero (Section IV-A)."""
+    m = MS.torus(1.0, 0.3, 12, 8)
+    d = dual_basis(m)
+    div = sp.coo_matrix((2 * d.bc_alpha * d.ref_area[d.bc_t], (d.bc_n, d.bc_t)), shape=(m.ne, d.nref)).toarray()
+    S = np.zeros((m.ne, m.nf))
+    S[np.arange(m.ne), m.ef[:, 0]] = 1
+    S[np.arange(m.ne), m.ef[:, 1]] = -1
+    assert np.abs(S.T @ div).max() < 1e-12
+    assert np.abs(div.sum(axis=1)).max() < 1e-12
+
+
+def test_static_operators_definiteness(pr1_ops):
+    """T_0^s SPD; T_0^h PSD of rank N_v - 1 on the BC space (Section III)."""
+    ops = pr1_ops
+    es = np.linalg.eigvalsh(ops.T0s)
+    eh = np.linalg.eigvalsh(ops.T0h)
+    assert es[0] > 0
+    assert eh[0] > -1e-12 * eh[-1]
+    assert int((eh > 1e-10 * eh[-1]).sum()) == ops.mesh.nv - 1
+
+
+def _lag_sum(mat, kmax_tail=None):
+    ne = mat.ne
+    out = np.zeros((ne, ne))
+    rows = np.repeat(np.arange(ne), np.diff(mat.rowptr))
+    for e in range(mat.col.size):
+        out[rows[e], mat.col[e]] += mat.val[mat.voff[e]:mat.voff[e] + mat.cnt[e]].sum()
+    return out
+
+
+def _tail_dense(mat):
+    ne = mat.ne
+    out = np.zeros((ne, ne))
+    rows = np.repeat(np.arange(ne), np.diff(mat.rowptr))
+    out[rows, mat.col] = mat.tc
+    return out
+
+
+@pytest.mark.parametrize("med", ["", "p"])
+def test_temporal_partition_identities(pr1_ops, med):
+    """Sums over lags fixed by the temporal bases (Section V-A, V-B):
+    sum_k h_0'(tau_k) = 0 -> sum_k T_k = 0; sum_k q_0'' = sum_k q_0' = 0 ->
+    sum_k K^_k = 0; sum_k h_0(tau_k) = 1 -> sum_k K_k = K_0, which also equals
+    (T_max/dt) times the constant tail of K~ (Section V-B-3)."""
+    ops = pr1_ops
+    sAT = _lag_sum(ops.mats["AT" + med])
+    sHK = _lag_sum(ops.mats["HK" + med])
+    sAK = _lag_sum(ops.mats["AK" + med])
+    tail = _tail_dense(ops.mats["TK" + med]) * ops.tmax / ops.dt
+    scale_T = np.abs(_lag_sum(ops.mats["TT" + med])).max() * ops.tmax / ops.dt
+    assert np.abs(sAT).max() < 1e-12 * scale_T
+    assert np.abs(sHK).max() < 1e-11 * np.abs(sAK).max() * ops.tmax / ops.dt
+    assert np.abs(sAK - tail).max() < 1e-12 * np.abs(tail).max()
+
+
+def test_lag_support_truncation(pr1_ops):
+    """A_k vanishes for k > k_max, A^_k for k > k_max + 1, A~_k for k > k_max - 1
+    (Section V-B); the K~ tail lies within lags <= k_max - 1."""
+    ops = pr1_ops
+    km = ops.kmax
+    for med in ("", "p"):
+        assert ops.mats["AT" + med].max_lag() <= km
+        assert ops.mats["AK" + med].max_lag() <= km
+        assert ops.mats["HT" + med].max_lag() <= km + 1
+        assert ops.mats["HK" + med].max_lag() <= km + 1
+        assert ops.mats["TT" + med].max_lag() <= km - 1
+        assert ops.mats["TK" + med].max_lag() <= km - 1
+    assert ops.kmax == 15 and ops.K == 16
+
+
+def test_static_single_layer_symmetry(pr1_ops):
+    """The lag sum of T~ is the static single layer (p_0 sums to one), which is
+    symmetric in (m, n): a check of the quadrature accuracy."""
+    s = _lag_sum(pr1_ops.mats["TT"])
+    assert np.abs(s - s.T).max() < 2e-3 * np.abs(s).max()
