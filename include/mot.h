@@ -1,0 +1,217 @@
+/*
+ * mot.h — C ABI of the GB300 marching-on-in-time (MOT) library for the
+ * Calderon-preconditioned, quasi-Helmholtz-regularised ("qHP") time-domain
+ * PMCHWT equation of Le, Muenger, Andriulli, Cools, "A Stable, Accurate, and
+ * Well-Conditioned Time-Domain PMCHWT Formulation" (arXiv 2510.07989).
+ *
+ * One MOT step solves Eq. (MOT):  Q_0 w_i = r_i - sum_{k>=1} Q_k w_{i-k},
+ * with Q_k = Q_k^ll + Q_k^ls + Q_k^sl + Q_k^ss built from the lagged
+ * interaction matrices of Section V-B, the static preconditioner
+ * T = P^{Sigma H} T_0^s P^{Sigma H} + P^Lambda T_0^h P^Lambda (Eq. (CP)),
+ * the Gram matrix G (Section III) and the quasi-Helmholtz projectors
+ * (Section IV-B). Everything runs on one CUDA device (sm_103a).
+ *
+ * Conventions
+ *   - All arrays are plain C arrays; "host" pointers are read during the call
+ *     and never retained (the library copies what it needs).
+ *   - Unknown layout for B right-hand sides: w[b][0][m] = u_m, w[b][1][m] = v_m,
+ *     m in canonical edge order (see mot_create).
+ *   - Floating point is IEEE binary64 unless stated.
+ *   - Every function returns MOT_OK (0) or a negative status; no C++ exception
+ *     crosses this boundary. mot_last_error() returns a message for the last
+ *     failing call on a handle.
+ *   - A handle is not thread safe; calls on one handle must be serialised.
+ */
+#ifndef MOT_H
+#define MOT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MOT_OK = 0,
+    MOT_EINVAL = -1,   /* bad argument: sizes, NaN/Inf, K too small, open mesh ... */
+    MOT_EOOM = -2,     /* device or host allocation failed */
+    MOT_ENOCONV = -3,  /* GMRES or CG reached its iteration limit (result kept, flagged) */
+    MOT_ECUDA = -4,    /* CUDA runtime error (message in mot_last_error) */
+    MOT_ESTATE = -5    /* call out of order (e.g. step before load_operators) */
+};
+
+enum { MOT_PREC_FP64 = 0, MOT_PREC_MIXED = 1 };
+
+typedef struct mot_handle mot_handle;
+
+/* Closed, outward-oriented triangle mesh (paper Section II). */
+typedef struct {
+    int32_t nv;            /* number of vertices */
+    const double* verts;   /* [nv][3] host */
+    int32_t nf;            /* number of triangles */
+    const int32_t* tris;   /* [nf][3] host, counter-clockwise seen from outside */
+} mot_mesh;
+
+/* Solver options; pass NULL for defaults. */
+typedef struct {
+    int32_t precision;     /* MOT_PREC_FP64 (default) */
+    int32_t device;        /* CUDA device ordinal, default 0 */
+    double gmres_tol;      /* relative residual of the Q_0 solve, default 1e-12 */
+    int32_t gmres_maxit;   /* default 200 */
+    double cg_tol;         /* relative residual of Laplacian / Gram solves, default 1e-14 */
+    int32_t cg_maxit;      /* default 5000 */
+} mot_options;
+
+/*
+ * Lag-window sparse matrix (one family / medium of Section V-B):
+ * for row m, entries e in [rowptr[m], rowptr[m+1]) hold column col[e] and
+ * values val[voff[e] .. voff[e] + cnt[e] - 1] for lags k0[e] .. k0[e]+cnt[e]-1.
+ * For K~ (Section V-B-3) tail_lag/tail_val (nullable otherwise) give a
+ * constant tail_val[e] for lags tail_lag[e] .. k_max - 1.
+ */
+typedef struct {
+    int64_t nent;
+    const int64_t* rowptr;   /* [ne+1] */
+    const int32_t* col;      /* [nent] */
+    const int32_t* k0;       /* [nent] */
+    const int32_t* cnt;      /* [nent] */
+    const int64_t* voff;     /* [nent] */
+    const double* val;       /* values */
+    const int32_t* tail_lag; /* [nent] or NULL */
+    const double* tail_val;  /* [nent] or NULL */
+} mot_lagmat;
+
+/*
+ * Every input of the MOT step (host pointers, copied by mot_load_operators).
+ *   mat[0..5]  exterior medium: A.T, A.K, Ah.T, Ah.K, At.T, At.K
+ *   mat[6..11] interior medium: same order.
+ *     A  : T_k, K_k        (h_0 basis, collocation at k dt; Section V-B-1)
+ *     Ah : T^_k, K^_k      (T_max d/dt of q_0; Section V-B-2)
+ *     At : T~_k, K~_k      ((1/T_max) d/dt^-1 of p_0; Section V-B-3)
+ *   T0s, T0h : static BC-space operators T_0^s, T_0^h (Section III), dense
+ *              row-major ne x ne.
+ *   G  : Gram matrix <n x f_m, g_n> (Section III), CSR ne x ne.
+ *   rhs_x, rhs_wf : RWG quadrature table [ne][nq][3] of points and
+ *              weight * area * f_m(x) (both triangles of each edge), used to
+ *              test the incident field (Section V-C) and for far fields.
+ */
+typedef struct {
+    mot_lagmat mat[12];
+    const double* T0s;
+    const double* T0h;
+    const int64_t* g_rowptr;
+    const int32_t* g_col;
+    const double* g_val;
+    int32_t nq;
+    const double* rhs_x;
+    const double* rhs_wf;
+} mot_operators;
+
+/* Gaussian plane wave of Eq. (hin): amplitude A, polarisation p, direction k,
+ * width w, arrival t0; the star right-hand side is forced to 0 for
+ * i dt > t_trunc (Section V-C). */
+typedef struct {
+    double A;
+    double p[3];
+    double k[3];
+    double w;
+    double t0;
+    double t_trunc;
+} mot_wave;
+
+typedef struct {
+    int32_t ne, nv, nf;
+    int32_t kmax;          /* ceil(T_max/dt) */
+    int32_t K;             /* history lags used (k_max + 1) */
+    int32_t B;             /* current batch size (0 before the first step) */
+    int64_t step;          /* steps completed */
+    double D, tmax, dt;
+    int32_t last_gmres_iters;   /* max over the batch, last step */
+    double last_gmres_resid;    /* max relative residual, last step */
+    int32_t last_cg_iters;      /* max CG iterations of any projector/Gram solve, last step */
+    int64_t device_bytes;       /* device memory held by the handle */
+    int64_t gpu_launches;       /* kernels launched by this handle so far */
+    double tile_fill;           /* nonzero fraction of the stored history tiles */
+    int64_t tile_count;         /* stored history tiles (all lags and families) */
+} mot_info;
+
+/*
+ * Create a solver for one scatterer (paper Section II).
+ *   mesh   : closed 2-manifold, outward orientation. The library builds the
+ *            canonical edge table: edges are vertex pairs (a<b) sorted
+ *            lexicographically, oriented v^- = a -> v^+ = b; c^+ is the
+ *            triangle left of that direction seen from outside.
+ *   eps_r, mu_r : interior material relative to the exterior (c = 1, eta = 1).
+ *   dt     : time step (> 0).
+ *   K      : number of history lags to keep; must be >= k_max + 1 with
+ *            k_max = ceil(T_max/dt), T_max = D / min(c, c') (Eq. (alpha)),
+ *            D = largest vertex distance.
+ * Errors: MOT_EINVAL (open/non-manifold mesh, eps_r/mu_r/dt <= 0, K too
+ * small), MOT_ECUDA, MOT_EOOM. On success *out owns device memory until
+ * mot_destroy.
+ */
+int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double dt, int K, const mot_options* opt,
+               mot_handle** out);
+
+/* Copy all operators to the device and build the internal block-sparse
+ * layout. Errors: MOT_EINVAL (NaN/Inf, lag beyond its family's range,
+ * index out of range), MOT_EOOM, MOT_ECUDA, MOT_ESTATE (called twice). */
+int mot_load_operators(mot_handle* h, const mot_operators* ops);
+
+/*
+ * Optional: frequencies (angular, rad per unit time) of the running Fourier
+ * transforms of the recovered loop and star currents (Eq. (dis_jm); the two
+ * parts are accumulated separately). Must be called before the first step.
+ */
+int mot_set_frequencies(mot_handle* h, int n_freq, const double* omega);
+
+/*
+ * Advance one MOT step for B plane waves (B <= 64, fixed after the first
+ * step until mot_reset). w_out (nullable) receives w_i as [B][2][ne];
+ * host or device memory (detected). stream: a cudaStream_t or NULL for the
+ * default stream. Errors: MOT_ENOCONV (GMRES/CG limit hit; w_i is the last
+ * iterate and the step counts), MOT_EINVAL, MOT_ESTATE, MOT_ECUDA.
+ */
+int mot_step(mot_handle* h, const mot_wave* waves, int B, double* w_out, void* stream);
+
+/* n_steps calls of mot_step; w_out (nullable) receives [n_steps][B][2][ne]. */
+int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, double* w_out, void* stream);
+
+/* Recovered currents of the last step, [B][4][ne]: j loop, j star, m loop,
+ * m star (Eq. (dis_jm)), host or device memory. */
+int mot_get_currents(mot_handle* h, double* out);
+
+/*
+ * Scattered far field (after stepping) in the exterior medium, normalised by
+ * the incident pulse spectrum at the origin, for every frequency set with
+ * mot_set_frequencies and every unit direction dirs[n_dir][3] (host):
+ *   E_inf(r) = (j k / 4 pi) [eta r x (r x N) + r x L],
+ *   N = int J^(y) e^{j k r.y}, L = int M^(y) e^{j k r.y},
+ * J^, M^ the exact Fourier transforms of the piecewise-constant currents.
+ * E_out (host): [B][n_freq][n_dir][3] complex as (re, im) pairs.
+ */
+int mot_fields(mot_handle* h, const mot_wave* waves, int n_dir, const double* dirs, double* E_out);
+
+/* Restart the march at step 0 (operators kept). */
+int mot_reset(mot_handle* h);
+
+/* Save / restore the march state (step index, history ring, Fourier sums).
+ * mot_save_state with buf == NULL returns the size in *size. */
+int mot_save_state(mot_handle* h, void* buf, size_t* size);
+int mot_load_state(mot_handle* h, const void* buf, size_t size);
+
+int mot_get_info(mot_handle* h, mot_info* info);
+
+/* Canonical edge table built by mot_create: ev[ne][2] (v^-, v^+),
+ * ef[ne][2] (c^+, c^-) (host output arrays). */
+int mot_get_edges(mot_handle* h, int32_t* ev, int32_t* ef);
+
+const char* mot_last_error(mot_handle* h);
+
+void mot_destroy(mot_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOT_H */

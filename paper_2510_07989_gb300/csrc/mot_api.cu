@@ -1,0 +1,1079 @@
+// C ABI of the GB300 MOT library: handle lifetime, topology, operator upload,
+// the MOT step pipeline and the batched GMRES solve of Q_0 (paper Eq. (MOT)).
+//
+// Step i (all on one stream, FP64):
+//   rho1, rho2                   <- incident field tested (Section V-C)
+//   s1, s2                       <- block-sparse history over lags 1..K
+//   b = LF(rho1 - s1, rho2 - s2), LF(y1, y2) = T^{SH} G^-1 y1 + T^L G^-1 P^{LH} y2
+//   w_i = GMRES(Q_0, b),  Q_0 w = LF(A_0 l + A^_0 s, A~_0 l + A_0 s),
+//         s = P^S w, l = w - s   (Section V-B product form, no dense Q_k)
+//   ring slot <- variants of l_i, s_i; currents and Fourier sums (Eq. (dis_jm))
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "mot_internal.h"
+
+#define MOT_API extern "C" __attribute__((visibility("default")))
+
+namespace mot {
+
+int fail(mot_handle* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+int cuda_fail(mot_handle* h, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (h) h->err = m;
+    return e == cudaErrorMemoryAllocation ? MOT_EOOM : MOT_ECUDA;
+}
+
+void* dalloc(mot_handle* h, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemset(p, 0, bytes);
+    h->device_bytes += (int64_t)bytes;
+    return p;
+}
+
+// extra launch wrappers (k_linalg.cu)
+void launch_pack2(mot_handle* h, const double* a, const double* b, int C, double* out, cudaStream_t s);
+void launch_unpack_q(mot_handle* h, const double* X, const double* P, int C, double* q1, double* q2, cudaStream_t s);
+void launch_far_field(mot_handle* h, int n_dir, const double* dirs, double* E, cudaStream_t s);
+void launch_pack_cur(mot_handle* h, double* out, cudaStream_t s);
+
+}  // namespace mot
+
+using namespace mot;
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);       \
+    } while (0)
+
+namespace {
+
+struct HostCsr {
+    int n = 0, m = 0;
+    std::vector<int> rp, ci;
+    std::vector<double> va;
+};
+
+int upload_csr(mot_handle* h, const HostCsr& A, DCsr& D) {
+    D.n = A.n;
+    D.m = A.m;
+    D.nnz = (int64_t)A.ci.size();
+    D.rowptr = (int*)dalloc(h, sizeof(int) * (A.n + 1));
+    D.col = (int*)dalloc(h, sizeof(int) * std::max<size_t>(1, A.ci.size()));
+    D.val = (double*)dalloc(h, sizeof(double) * std::max<size_t>(1, A.va.size()));
+    if (!D.rowptr || !D.col || !D.val) return fail(h, MOT_EOOM, "device allocation (CSR)");
+    CK(cudaMemcpy(D.rowptr, A.rp.data(), sizeof(int) * (A.n + 1), cudaMemcpyHostToDevice));
+    if (!A.ci.empty()) {
+        CK(cudaMemcpy(D.col, A.ci.data(), sizeof(int) * A.ci.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(D.val, A.va.data(), sizeof(double) * A.va.size(), cudaMemcpyHostToDevice));
+    }
+    return MOT_OK;
+}
+
+HostCsr csr_from_triplets(int n, int m, std::vector<std::tuple<int, int, double>>& t) {
+    std::sort(t.begin(), t.end(), [](const auto& a, const auto& b) {
+        return std::get<0>(a) != std::get<0>(b) ? std::get<0>(a) < std::get<0>(b) : std::get<1>(a) < std::get<1>(b);
+    });
+    HostCsr A;
+    A.n = n;
+    A.m = m;
+    A.rp.assign(n + 1, 0);
+    for (size_t i = 0; i < t.size(); i++) {
+        int r = std::get<0>(t[i]), c = std::get<1>(t[i]);
+        double v = std::get<2>(t[i]);
+        if (!A.ci.empty() && A.rp[r + 1] > 0 && (int)A.ci.size() > 0 && i > 0 && std::get<0>(t[i - 1]) == r &&
+            std::get<1>(t[i - 1]) == c) {
+            A.va.back() += v;
+            continue;
+        }
+        A.ci.push_back(c);
+        A.va.push_back(v);
+        A.rp[r + 1]++;
+    }
+    for (int r = 0; r < n; r++) A.rp[r + 1] += A.rp[r];
+    return A;
+}
+
+uint64_t spread3(uint64_t x) {
+    x &= 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+
+// ---------------------------------------------------------------- step pieces
+struct Work {
+    double *rho1, *rho2, *s1, *s2, *y1, *y2, *b, *x, *w, *r, *sig, *ell, *tmp, *z2;
+    double *kry;              // [2][3] block vectors
+    double *Y4, *GY4, *X4, *PX4;  // 4B-column block vectors
+    double *q1, *q2, *t1, *t2, *dd, *pd;
+    double *fvec, *zvec;      // faces / vertices x 4B
+    double *cgw;              // CG scratch 4 x maxN x 4B
+    double *hc1, *hc2, *hsum, *nrm, *beta, *ygm;
+};
+
+Work work_of(mot_handle* h) {
+    Work W;
+    const size_t bv = (size_t)h->npad * 2 * h->B;
+    const size_t bv4 = 2 * bv;
+    const int maxN = std::max(std::max(h->npad, h->nf), h->nv);
+    double* p = h->d_work;
+    auto take = [&](size_t n) {
+        double* q = p;
+        p += (n + 31) / 32 * 32;
+        return q;
+    };
+    W.rho1 = take(bv);
+    W.rho2 = take(bv);
+    W.s1 = take(bv);
+    W.s2 = take(bv);
+    W.y1 = take(bv);
+    W.y2 = take(bv);
+    W.b = take(bv);
+    W.x = take(bv);
+    W.w = take(bv);
+    W.r = take(bv);
+    W.sig = take(bv);
+    W.ell = take(bv);
+    W.tmp = take(bv);
+    W.z2 = take(bv);
+    W.kry = take(6 * bv);
+    W.Y4 = take(bv4);
+    W.GY4 = take(bv4);
+    W.X4 = take(bv4);
+    W.PX4 = take(bv4);
+    W.q1 = take(bv);
+    W.q2 = take(bv);
+    W.t1 = take(bv);
+    W.t2 = take(bv);
+    W.dd = take(bv);
+    W.pd = take(bv);
+    W.fvec = take((size_t)std::max(h->nf, h->nv) * 4 * h->B);
+    W.zvec = take((size_t)std::max(h->nf, h->nv) * 4 * h->B);
+    W.cgw = take((size_t)4 * maxN * 4 * h->B);
+    const size_t gm = (size_t)(h->gm_m + 1) * h->B;
+    W.hc1 = take(gm);
+    W.hc2 = take(gm);
+    W.hsum = take(gm);
+    W.nrm = take(h->B);
+    W.beta = take(h->B);
+    W.ygm = take(gm);
+    return W;
+}
+
+size_t work_doubles(mot_handle* h) {
+    const size_t bv = (size_t)h->npad * 2 * h->B;
+    const int maxN = std::max(std::max(h->npad, h->nf), h->nv);
+    const size_t gm = (size_t)(h->gm_m + 1) * h->B;
+    size_t n = 0;
+    auto add = [&](size_t k) { n += (k + 31) / 32 * 32; };
+    for (int i = 0; i < 14; i++) add(bv);
+    add(6 * bv);
+    for (int i = 0; i < 4; i++) add(2 * bv);
+    for (int i = 0; i < 6; i++) add(bv);
+    add((size_t)std::max(h->nf, h->nv) * 4 * h->B);
+    add((size_t)std::max(h->nf, h->nv) * 4 * h->B);
+    add((size_t)4 * maxN * 4 * h->B);
+    add(gm);
+    add(gm);
+    add(gm);
+    add(h->B);
+    add(h->B);
+    add(gm);
+    return n;
+}
+
+// out = P^Sigma x  (C = 2B columns); Sigma^T x -> CG on Sigma^T Sigma -> Sigma z
+void project_sigma(mot_handle* h, const Work& W, const double* x, double* out, cudaStream_t s) {
+    const int C = 2 * h->B;
+    launch_sigma_t(h, x, C, W.fvec, s);
+    launch_cg(h, h->Lf, nullptr, W.fvec, C, W.zvec, W.cgw, s);
+    launch_sigma(h, W.zvec, C, out, s);
+}
+
+// out = P^Lambda x for C columns
+void project_lambda(mot_handle* h, const Work& W, const double* x, int C, double* out, cudaStream_t s) {
+    launch_lambda_t(h, x, C, W.fvec, s);
+    launch_cg(h, h->Lv, nullptr, W.fvec, C, W.zvec, W.cgw, s);
+    launch_lambda(h, W.zvec, C, out, s);
+}
+
+// out = T^{SH} G^-1 y1 + T^L G^-1 P^{LH} y2   (Eq. (CP), (reg_DCP_PMCHWT))
+void left_factor(mot_handle* h, const Work& W, const double* y1, const double* y2, double* out, cudaStream_t s) {
+    const int C = 2 * h->B;
+    const int n = h->npad * C;
+    project_sigma(h, W, y2, W.tmp, s);
+    launch_axpby(h, n, 1.0, y2, -1.0, W.tmp, W.z2, s);  // z2 = P^{LH} y2
+    launch_pack2(h, y1, W.z2, C, W.Y4, s);
+    launch_spmv(h, h->Gt, W.Y4, 2 * C, W.GY4, s);        // G^T Y
+    launch_cg(h, h->G, &h->Gt, W.GY4, 2 * C, W.X4, W.cgw, s);  // (G^T G) X = G^T Y
+    project_lambda(h, W, W.X4, 2 * C, W.PX4, s);
+    launch_unpack_q(h, W.X4, W.PX4, C, W.q1, W.q2, s);  // q1 = P^{SH} x1, q2 = P^L x2
+    launch_gemm(h, h->d_T0s, W.q1, C, W.t1, s);
+    launch_gemm(h, h->d_T0h, W.q2, C, W.t2, s);
+    launch_axpby(h, n, 1.0, W.t2, -1.0, W.t1, W.dd, s);
+    project_lambda(h, W, W.dd, C, W.pd, s);
+    launch_axpby(h, n, 1.0, W.t1, 1.0, W.pd, out, s);   // P^{SH} t1 + P^L t2
+}
+
+// out = Q_0 v in product form
+void apply_q0(mot_handle* h, const Work& W, const double* v, double* out, cudaStream_t s) {
+    const int n = h->npad * 2 * h->B;
+    const size_t bv = (size_t)n;
+    project_sigma(h, W, v, W.sig, s);
+    launch_axpby(h, n, 1.0, v, -1.0, W.sig, W.ell, s);
+    launch_variants(h, W.ell, W.kry, h->eta, h->etap, s);
+    launch_variants(h, W.sig, W.kry + 3 * bv, h->eta, h->etap, s);
+    launch_history(h, h->lag0, h->d_tiles, nullptr, nullptr, W.kry, 1, 0, W.y1, W.y2, s);
+    left_factor(h, W, W.y1, W.y2, out, s);
+}
+
+int gmres(mot_handle* h, const Work& W, const double* b, double* x, cudaStream_t s) {
+    const int B = h->B;
+    const size_t bv = (size_t)h->npad * 2 * B;
+    const int m = h->gm_m;
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * bv, s));
+    launch_gm_norm(h, b, W.beta, s);
+    launch_gm_init(h, W.beta, 1, s);
+    launch_gm_scale(h, b, W.beta, h->d_V, s);
+    int total = 0;
+    bool converged = false;
+    std::vector<int> act(B);
+    for (int cycle = 0; !converged && total < h->opt.gmres_maxit; cycle++) {
+        int jend = 0;
+        for (int j = 0; j < m && total < h->opt.gmres_maxit; j++) {
+            const double* Vj = h->d_V + (size_t)j * bv;
+            apply_q0(h, W, Vj, W.w, s);
+            launch_gm_dots(h, h->d_V, j + 1, W.w, W.hc1, s);
+            launch_gm_update(h, h->d_V, j + 1, W.hc1, W.w, s);
+            launch_gm_dots(h, h->d_V, j + 1, W.w, W.hc2, s);
+            launch_gm_update(h, h->d_V, j + 1, W.hc2, W.w, s);
+            launch_axpby(h, (j + 1) * B, 1.0, W.hc1, 1.0, W.hc2, W.hsum, s);
+            launch_gm_norm(h, W.w, W.nrm, s);
+            launch_gm_arnoldi_finish(h, j, W.hsum, W.nrm, s);
+            launch_gm_scale(h, W.w, W.nrm, h->d_V + (size_t)(j + 1) * bv, s);
+            CK(cudaMemcpyAsync(act.data(), h->d_gm_active, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            total++;
+            jend = j + 1;
+            bool any = false;
+            for (int k = 0; k < B; k++) any |= act[k] != 0;
+            if (!any) {
+                converged = true;
+                break;
+            }
+        }
+        if (jend > 0) launch_gm_solve_update(h, W.ygm, x, s);
+        if (converged || total >= h->opt.gmres_maxit) break;
+        // restart from the true residual
+        apply_q0(h, W, x, W.r, s);
+        launch_axpby(h, (int)bv, 1.0, b, -1.0, W.r, W.r, s);
+        launch_gm_norm(h, W.r, W.beta, s);
+        launch_gm_init(h, W.beta, 0, s);
+        launch_gm_scale(h, W.r, W.beta, h->d_V, s);
+    }
+    std::vector<double> res(B);
+    CK(cudaMemcpyAsync(res.data(), h->d_resid, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->last_gmres_iters = total;
+    h->last_gmres_resid = 0;
+    for (double r : res) h->last_gmres_resid = std::max(h->last_gmres_resid, r);
+    return converged ? MOT_OK : fail(h, MOT_ENOCONV, "GMRES reached its iteration limit");
+}
+
+int ensure_state(mot_handle* h, int B) {
+    if (h->B == B && h->d_ring) return MOT_OK;
+    if (h->B != 0 && h->B != B) return fail(h, MOT_EINVAL, "batch size changed without mot_reset");
+    h->B = B;
+    const size_t bv = (size_t)h->npad * 2 * B;
+    h->gm_m = std::min(std::max(h->opt.gmres_maxit, 1), 100);
+    h->d_waves = (double*)dalloc(h, sizeof(double) * 10 * B);
+    h->d_ring = (double*)dalloc(h, sizeof(double) * (size_t)h->R * 6 * bv);
+    h->d_win = (double*)dalloc(h, sizeof(double) * (size_t)(h->max_tail_lag + 1) * bv);
+    h->d_cur = (double*)dalloc(h, sizeof(double) * 4 * (size_t)h->npad * B);
+    h->d_dft = (double*)dalloc(h, sizeof(double) * std::max(1, h->nfreq) * 4 * (size_t)h->npad * B * 2);
+    h->work_bytes = sizeof(double) * work_doubles(h);
+    h->d_work = (double*)dalloc(h, h->work_bytes);
+    int maxch = std::max(h->hist.nchunks, h->lag0.nchunks);
+    h->partial_bytes = sizeof(double) * (size_t)std::max(1, maxch) * 2 * MOT_TILE * 2 * B;
+    h->d_partial = (double*)dalloc(h, h->partial_bytes);
+    h->d_V = (double*)dalloc(h, sizeof(double) * (size_t)(h->gm_m + 1) * bv);
+    h->d_H = (double*)dalloc(h, sizeof(double) * (size_t)B * (h->gm_m + 1) * h->gm_m);
+    h->d_g = (double*)dalloc(h, sizeof(double) * (size_t)B * (h->gm_m + 1));
+    h->d_cs = (double*)dalloc(h, sizeof(double) * (size_t)B * h->gm_m);
+    h->d_sn = (double*)dalloc(h, sizeof(double) * (size_t)B * h->gm_m);
+    h->red_bytes = sizeof(double) * (size_t)((h->npad + 255) / 256 + 1) * (h->gm_m + 1) * B;
+    h->d_red = (double*)dalloc(h, h->red_bytes);
+    h->d_resid = (double*)dalloc(h, sizeof(double) * B);
+    h->d_gm_active = (int*)dalloc(h, sizeof(int) * B);
+    h->d_gm_jend = (int*)dalloc(h, sizeof(int) * B);
+    h->d_gm_bnorm = (double*)dalloc(h, sizeof(double) * B);
+    if (!h->d_waves || !h->d_ring || !h->d_win || !h->d_cur || !h->d_dft || !h->d_work || !h->d_partial ||
+        !h->d_V || !h->d_H || !h->d_g || !h->d_cs || !h->d_sn || !h->d_red || !h->d_resid || !h->d_gm_active ||
+        !h->d_gm_jend || !h->d_gm_bnorm)
+        return fail(h, MOT_EOOM, "device allocation of the march state");
+    h->h_waves.assign(10 * B, NAN);
+    return MOT_OK;
+}
+
+void free_state(mot_handle* h) {
+    void* ptrs[] = {h->d_waves, h->d_ring, h->d_win, h->d_cur, h->d_dft, h->d_work, h->d_partial, h->d_V, h->d_H,
+                    h->d_g, h->d_cs, h->d_sn, h->d_red, h->d_resid, h->d_gm_active, h->d_gm_jend, h->d_gm_bnorm};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->d_waves = h->d_ring = h->d_win = h->d_cur = h->d_dft = h->d_work = h->d_partial = nullptr;
+    h->d_V = h->d_H = h->d_g = h->d_cs = h->d_sn = h->d_red = h->d_resid = nullptr;
+    h->d_gm_active = h->d_gm_jend = nullptr;
+    h->d_gm_bnorm = nullptr;
+    h->B = 0;
+    h->step = 0;
+}
+
+int check_waves(mot_handle* h, const mot_wave* waves, int B) {
+    for (int b = 0; b < B; b++) {
+        const mot_wave& w = waves[b];
+        double v[10] = {w.A, w.p[0], w.p[1], w.p[2], w.k[0], w.k[1], w.k[2], w.w, w.t0, w.t_trunc};
+        for (double x : v)
+            if (!std::isfinite(x)) return fail(h, MOT_EINVAL, "non-finite plane-wave parameter");
+        if (!(w.w > 0)) return fail(h, MOT_EINVAL, "plane-wave width must be > 0");
+    }
+    return MOT_OK;
+}
+
+int upload_waves(mot_handle* h, const mot_wave* waves, int B, cudaStream_t s) {
+    std::vector<double> v(10 * B);
+    for (int b = 0; b < B; b++) {
+        const mot_wave& w = waves[b];
+        double t[10] = {w.A, w.p[0], w.p[1], w.p[2], w.k[0], w.k[1], w.k[2], w.w, w.t0, w.t_trunc};
+        memcpy(&v[10 * b], t, sizeof t);
+    }
+    if (memcmp(v.data(), h->h_waves.data(), sizeof(double) * 10 * B) != 0) {
+        h->h_waves = v;
+        CK(cudaMemcpyAsync(h->d_waves, h->h_waves.data(), sizeof(double) * 10 * B, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return MOT_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int do_step(mot_handle* h, cudaStream_t s) {
+    Work W = work_of(h);
+    const long long i = h->step + 1;
+    const int n = h->npad * 2 * h->B;
+    const size_t bv = (size_t)n;
+    CK(cudaMemsetAsync(h->d_cg_iters, 0, 2 * sizeof(int), s));
+    launch_rhs(h, i, W.rho1, W.rho2, s);
+    if (i >= 2) {
+        launch_window_sums(h, i, s);
+        launch_history(h, h->hist, h->d_tiles, h->d_ring, h->d_win, nullptr, 0, i, W.s1, W.s2, s);
+        launch_axpby(h, n, 1.0, W.rho1, -1.0, W.s1, W.y1, s);
+        launch_axpby(h, n, 1.0, W.rho2, -1.0, W.s2, W.y2, s);
+    } else {
+        launch_axpby(h, n, 1.0, W.rho1, 0.0, nullptr, W.y1, s);
+        launch_axpby(h, n, 1.0, W.rho2, 0.0, nullptr, W.y2, s);
+    }
+    left_factor(h, W, W.y1, W.y2, W.b, s);
+    int st = gmres(h, W, W.b, W.x, s);
+    if (st != MOT_OK && st != MOT_ENOCONV) return st;
+    // ring slot i: variants of l_i and s_i
+    project_sigma(h, W, W.x, W.sig, s);
+    launch_axpby(h, n, 1.0, W.x, -1.0, W.sig, W.ell, s);
+    const int slot = (int)(i % h->R);
+    launch_variants(h, W.ell, h->d_ring + ((size_t)slot * 2 + 0) * 3 * bv, h->eta, h->etap, s);
+    launch_variants(h, W.sig, h->d_ring + ((size_t)slot * 2 + 1) * 3 * bv, h->eta, h->etap, s);
+    h->step = i;
+    launch_recover(h, i, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_cg_iters, h->d_cg_iters, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h->last_cg_iters = h->h_cg_iters[0];
+    if (h->h_cg_iters[1] > 0) return fail(h, MOT_ENOCONV, "a projector or Gram CG solve reached its iteration limit");
+    return st;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double dt, int K, const mot_options* opt,
+                       mot_handle** out) {
+    if (!out) return MOT_EINVAL;
+    *out = nullptr;
+    mot_handle* h = new mot_handle();
+    h->opt.precision = MOT_PREC_FP64;
+    h->opt.device = 0;
+    h->opt.gmres_tol = 1e-12;
+    h->opt.gmres_maxit = 200;
+    h->opt.cg_tol = 1e-14;
+    h->opt.cg_maxit = 5000;
+    if (opt) {
+        h->opt.precision = opt->precision;
+        h->opt.device = opt->device;
+        if (opt->gmres_tol > 0) h->opt.gmres_tol = opt->gmres_tol;
+        if (opt->gmres_maxit > 0) h->opt.gmres_maxit = opt->gmres_maxit;
+        if (opt->cg_tol > 0) h->opt.cg_tol = opt->cg_tol;
+        if (opt->cg_maxit > 0) h->opt.cg_maxit = opt->cg_maxit;
+    }
+    auto bad = [&](const char* m) {
+        h->err = m;
+        *out = h;  // keep the handle so the caller can read the message
+        return MOT_EINVAL;
+    };
+    if (!mesh || !mesh->verts || !mesh->tris || mesh->nv < 4 || mesh->nf < 4) return bad("mesh missing or too small");
+    if (!(eps_r > 0) || !(mu_r > 0) || !(dt > 0) || !std::isfinite(eps_r) || !std::isfinite(mu_r) || !std::isfinite(dt))
+        return bad("eps_r, mu_r and dt must be finite and > 0");
+    if (h->opt.precision != MOT_PREC_FP64) return bad("only MOT_PREC_FP64 is available in this build");
+    h->nv = mesh->nv;
+    h->nf = mesh->nf;
+    h->verts.assign(mesh->verts, mesh->verts + 3 * (size_t)h->nv);
+    h->tris.assign(mesh->tris, mesh->tris + 3 * (size_t)h->nf);
+    for (double v : h->verts)
+        if (!std::isfinite(v)) return bad("non-finite vertex coordinate");
+    for (int t : h->tris)
+        if (t < 0 || t >= h->nv) return bad("triangle vertex index out of range");
+    // canonical edges: directed a->b of every face; the face is c+ of (a,b) if a < b
+    std::map<std::pair<int, int>, std::pair<int, int>> dir;  // (a,b) -> (face, opposite)
+    for (int f = 0; f < h->nf; f++) {
+        const int* t = &h->tris[3 * f];
+        for (int j = 0; j < 3; j++) {
+            int a = t[j], b = t[(j + 1) % 3], o = t[(j + 2) % 3];
+            if (a == b) return bad("degenerate triangle");
+            if (!dir.emplace(std::make_pair(a, b), std::make_pair(f, o)).second)
+                return bad("repeated directed edge: mesh is non-manifold or inconsistently oriented");
+        }
+    }
+    for (auto& kv : dir) {
+        int a = kv.first.first, b = kv.first.second;
+        auto it = dir.find({b, a});
+        if (it == dir.end()) return bad("open or inconsistently oriented mesh");
+        if (a < b) {
+            h->ev.push_back(a);
+            h->ev.push_back(b);
+            h->ef.push_back(kv.second.first);
+            h->ef.push_back(it->second.first);
+            h->eo.push_back(kv.second.second);
+            h->eo.push_back(it->second.second);
+        }
+    }
+    h->ne = (int)h->ev.size() / 2;
+    if (2 * h->ne != 3 * h->nf) return bad("edge count is not 3F/2");
+    // material, D, T_max, k_max (Eq. (alpha), Section V-B)
+    h->eps_r = eps_r;
+    h->mu_r = mu_r;
+    h->dt = dt;
+    h->c = 1.0;
+    h->eta = 1.0;
+    h->cp = 1.0 / sqrt(eps_r * mu_r);
+    h->etap = sqrt(mu_r / eps_r);
+    double D2 = 0;
+    for (int a = 0; a < h->nv; a++)
+        for (int b = a + 1; b < h->nv; b++) {
+            double d0 = h->verts[3 * a] - h->verts[3 * b], d1 = h->verts[3 * a + 1] - h->verts[3 * b + 1],
+                   d2 = h->verts[3 * a + 2] - h->verts[3 * b + 2];
+            D2 = std::max(D2, d0 * d0 + d1 * d1 + d2 * d2);
+        }
+    h->D = sqrt(D2);
+    h->tmax = h->D / std::min(h->c, h->cp);
+    double r = h->tmax / dt;
+    double rn = std::round(r);
+    h->kmax = (fabs(r - rn) < 1e-12 * std::max(1.0, r)) ? (int)rn : (int)ceil(r);
+    if (K < h->kmax + 1) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "K = %d is smaller than k_max + 1 = %d", K, h->kmax + 1);
+        return bad(buf);
+    }
+    h->K = h->kmax + 1;
+    h->R = h->K + 1;
+    // Morton order of the edge midpoints (internal row order)
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int v = 0; v < h->nv; v++)
+        for (int d = 0; d < 3; d++) {
+            lo[d] = std::min(lo[d], h->verts[3 * v + d]);
+            hi[d] = std::max(hi[d], h->verts[3 * v + d]);
+        }
+    std::vector<std::pair<uint64_t, int>> keys(h->ne);
+    for (int e = 0; e < h->ne; e++) {
+        uint64_t code = 0;
+        for (int d = 0; d < 3; d++) {
+            double m = 0.5 * (h->verts[3 * h->ev[2 * e] + d] + h->verts[3 * h->ev[2 * e + 1] + d]);
+            double u = (hi[d] > lo[d]) ? (m - lo[d]) / (hi[d] - lo[d]) : 0.0;
+            uint64_t q = (uint64_t)std::min(2097151.0, std::max(0.0, u * 2097151.0));
+            code |= spread3(q) << d;
+        }
+        keys[e] = {code, e};
+    }
+    std::sort(keys.begin(), keys.end());
+    h->perm.resize(h->ne);
+    h->iperm.resize(h->ne);
+    for (int p = 0; p < h->ne; p++) {
+        h->perm[p] = keys[p].second;
+        h->iperm[keys[p].second] = p;
+    }
+    h->npad = (h->ne + MOT_TILE - 1) / MOT_TILE * MOT_TILE;
+    h->nrb = h->npad / MOT_TILE;
+    // device
+    cudaError_t ce = cudaSetDevice(h->opt.device);
+    if (ce != cudaSuccess) {
+        *out = h;
+        return cuda_fail(h, ce, "cudaSetDevice");
+    }
+    h->dev = h->opt.device;
+    // incidence on the internal order
+    std::vector<int> efi(2 * h->ne), evi(2 * h->ne);
+    for (int p = 0; p < h->ne; p++) {
+        int e = h->perm[p];
+        efi[2 * p] = h->ef[2 * e];
+        efi[2 * p + 1] = h->ef[2 * e + 1];
+        evi[2 * p] = h->ev[2 * e];
+        evi[2 * p + 1] = h->ev[2 * e + 1];
+    }
+    std::vector<int> fe(3 * h->nf, -1);
+    std::vector<double> fs(3 * h->nf, 0.0);
+    std::vector<int> fill(h->nf, 0);
+    std::vector<std::tuple<int, int, double>> tv, tlf, tlv;
+    for (int p = 0; p < h->ne; p++) {
+        for (int side = 0; side < 2; side++) {
+            int f = efi[2 * p + side];
+            int k = fill[f]++;
+            if (k >= 3) return bad("face with more than three edges");
+            fe[3 * f + k] = p;
+            fs[3 * f + k] = side == 0 ? 1.0 : -1.0;
+        }
+        tv.emplace_back(evi[2 * p + 1], p, 1.0);
+        tv.emplace_back(evi[2 * p], p, -1.0);
+        int fp = efi[2 * p], fm = efi[2 * p + 1];
+        tlf.emplace_back(fp, fp, 1.0);
+        tlf.emplace_back(fm, fm, 1.0);
+        tlf.emplace_back(fp, fm, -1.0);
+        tlf.emplace_back(fm, fp, -1.0);
+        int vm = evi[2 * p], vp = evi[2 * p + 1];
+        tlv.emplace_back(vp, vp, 1.0);
+        tlv.emplace_back(vm, vm, 1.0);
+        tlv.emplace_back(vp, vm, -1.0);
+        tlv.emplace_back(vm, vp, -1.0);
+    }
+    HostCsr VE = csr_from_triplets(h->nv, h->ne, tv);
+    HostCsr LF = csr_from_triplets(h->nf, h->nf, tlf);
+    HostCsr LV = csr_from_triplets(h->nv, h->nv, tlv);
+    h->d_edge_faces = (int*)dalloc(h, sizeof(int) * 2 * h->ne);
+    h->d_edge_verts = (int*)dalloc(h, sizeof(int) * 2 * h->ne);
+    h->d_face_edges = (int*)dalloc(h, sizeof(int) * 3 * h->nf);
+    h->d_face_sgn = (double*)dalloc(h, sizeof(double) * 3 * h->nf);
+    h->d_iperm = (int*)dalloc(h, sizeof(int) * h->ne);
+    h->d_cg_iters = (int*)dalloc(h, sizeof(int) * 4);
+    *out = h;
+    if (!h->d_edge_faces || !h->d_edge_verts || !h->d_face_edges || !h->d_face_sgn || !h->d_iperm || !h->d_cg_iters)
+        return fail(h, MOT_EOOM, "device allocation (topology)");
+    CK(cudaMemcpy(h->d_edge_faces, efi.data(), sizeof(int) * 2 * h->ne, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_edge_verts, evi.data(), sizeof(int) * 2 * h->ne, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_face_edges, fe.data(), sizeof(int) * 3 * h->nf, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_face_sgn, fs.data(), sizeof(double) * 3 * h->nf, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_iperm, h->iperm.data(), sizeof(int) * h->ne, cudaMemcpyHostToDevice));
+    CK(cudaMallocHost(&h->h_cg_iters, sizeof(int) * 4));
+    int st;
+    if ((st = upload_csr(h, VE, h->vtx_edges)) != MOT_OK) return st;
+    if ((st = upload_csr(h, LF, h->Lf)) != MOT_OK) return st;
+    if ((st = upload_csr(h, LV, h->Lv)) != MOT_OK) return st;
+    return MOT_OK;
+}
+
+namespace {
+
+// tile kinds: 0 A.T ext, 1 A.T int, 2 A.K (ext+int), 3 Ah.T ext, 4 Ah.T int, 5 Ah.K, 6 At.T ext, 7 At.T int,
+// 8 At.K explicit, 9 At.K tails (window slices)
+constexpr int NTK = 10;
+const int kMatKind[12] = {0, 2, 3, 5, 6, 8, 1, 2, 4, 5, 7, 8};
+const int kKindVariant[NTK] = {0, 1, 2, 0, 1, 2, 0, 1, 2, 2};
+const int kKindFamily[NTK] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3};  // 0 A, 1 Ah, 2 At, 3 tail
+
+int build_tiles(mot_handle* h, const mot_operators* ops) {
+    const int T = MOT_TILE;
+    const int nrb = h->nrb;
+    const int L = h->kmax + 2;  // lags 0 .. kmax+1
+    std::vector<int> id((size_t)NTK * L * nrb * nrb, -1);
+    auto key = [&](int kind, int k, int rb, int cb) { return (((size_t)kind * L + k) * nrb + rb) * nrb + cb; };
+    int max_tail = 0;
+    // pass 1: validate and mark occupied tiles
+    for (int mi = 0; mi < 12; mi++) {
+        const mot_lagmat& M = ops->mat[mi];
+        const int kind = kMatKind[mi];
+        const int fam = kKindFamily[kind];
+        const int lagmax = fam == 0 ? h->kmax : fam == 1 ? h->kmax + 1 : h->kmax - 1;
+        if (M.nent > 0 && (!M.rowptr || !M.col || !M.k0 || !M.cnt || !M.voff || !M.val))
+            return fail(h, MOT_EINVAL, "lag matrix with missing arrays");
+        if (M.nent > 0 && M.rowptr[h->ne] != M.nent) return fail(h, MOT_EINVAL, "lag matrix rowptr[ne] != nent");
+        const bool tails = (mi == 5 || mi == 11) && M.tail_lag && M.tail_val;
+        for (int m = 0; m < h->ne && M.nent > 0; m++) {
+            const int rb = h->iperm[m] / T;
+            for (int64_t e = M.rowptr[m]; e < M.rowptr[m + 1]; e++) {
+                const int n = M.col[e];
+                if (n < 0 || n >= h->ne) return fail(h, MOT_EINVAL, "lag matrix column out of range");
+                const int cb = h->iperm[n] / T;
+                const int k0 = M.k0[e], c = M.cnt[e];
+                if (k0 < 0 || c < 0) return fail(h, MOT_EINVAL, "negative lag window");
+                for (int k = k0; k < k0 + c; k++) {
+                    const double v = M.val[M.voff[e] + (k - k0)];
+                    if (!std::isfinite(v)) return fail(h, MOT_EINVAL, "non-finite operator value");
+                    if (k > lagmax) {
+                        if (fam == 2) continue;  // explicit truncation of A~ (Section V-B-3)
+                        if (v != 0.0) return fail(h, MOT_EINVAL, "operator lag beyond its family's range");
+                        continue;
+                    }
+                    if (v == 0.0) continue;
+                    size_t kk = key(kind, k, rb, cb);
+                    if (id[kk] < 0) id[kk] = -2;
+                }
+                if (tails) {
+                    const int a = M.tail_lag[e];
+                    const double v = M.tail_val[e];
+                    if (!std::isfinite(v)) return fail(h, MOT_EINVAL, "non-finite tail value");
+                    if (a >= 1 && a <= h->kmax - 1 && v != 0.0) {
+                        size_t kk = key(9, a, rb, cb);
+                        if (id[kk] < 0) id[kk] = -2;
+                        max_tail = std::max(max_tail, a);
+                    }
+                }
+            }
+        }
+    }
+    int64_t nt = 0;
+    for (auto& v : id)
+        if (v == -2) v = (int)nt++;
+    h->ntiles = nt;
+    h->max_tail_lag = max_tail;
+    std::vector<double> tiles((size_t)nt * T * T, 0.0);
+    // pass 2: fill (row-block ranges in parallel threads)
+    auto fill = [&](int tid, int nth) {
+        for (int mi = 0; mi < 12; mi++) {
+            const mot_lagmat& M = ops->mat[mi];
+            const int kind = kMatKind[mi];
+            const int fam = kKindFamily[kind];
+            const int lagmax = fam == 0 ? h->kmax : fam == 1 ? h->kmax + 1 : h->kmax - 1;
+            const bool tails = (mi == 5 || mi == 11) && M.tail_lag && M.tail_val;
+            for (int m = 0; m < h->ne && M.nent > 0; m++) {
+                const int p = h->iperm[m];
+                const int rb = p / T;
+                if (rb % nth != tid) continue;
+                const int r = p - rb * T;
+                for (int64_t e = M.rowptr[m]; e < M.rowptr[m + 1]; e++) {
+                    const int q = h->iperm[M.col[e]];
+                    const int cb = q / T, cc = q - cb * T;
+                    for (int k = M.k0[e]; k < M.k0[e] + M.cnt[e] && k <= lagmax; k++) {
+                        const double v = M.val[M.voff[e] + (k - M.k0[e])];
+                        if (v == 0.0) continue;
+                        tiles[(size_t)id[key(kind, k, rb, cb)] * T * T + r * T + cc] += v;
+                    }
+                    if (tails) {
+                        const int a = M.tail_lag[e];
+                        const double v = M.tail_val[e];
+                        if (a >= 1 && a <= h->kmax - 1 && v != 0.0)
+                            tiles[(size_t)id[key(9, a, rb, cb)] * T * T + r * T + cc] += v;
+                    }
+                }
+            }
+        }
+    };
+    int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nth; t++) th.emplace_back(fill, t, nth);
+    for (auto& t : th) t.join();
+    int64_t nz = 0;
+    for (double v : tiles) nz += v != 0.0;
+    h->tile_fill = nt ? (double)nz / ((double)nt * T * T) : 0.0;
+    // task lists
+    std::vector<HistTask> th_hist, th_lag0;
+    std::vector<int> rb_hist, rb_lag0;
+    for (int kind = 0; kind < NTK; kind++)
+        for (int k = 0; k < L; k++)
+            for (int rb = 0; rb < nrb; rb++)
+                for (int cb = 0; cb < nrb; cb++) {
+                    int t = id[key(kind, k, rb, cb)];
+                    if (t < 0) continue;
+                    const int fam = kKindFamily[kind], var = kKindVariant[kind];
+                    auto push = [&](int part, int outi) {
+                        HistTask tk{t, cb, k, part | (var << 2) | (outi << 4)};
+                        if (k == 0 && fam != 3) {
+                            th_lag0.push_back(tk);
+                            rb_lag0.push_back(rb);
+                        } else {
+                            th_hist.push_back(tk);
+                            rb_hist.push_back(rb);
+                        }
+                    };
+                    if (fam == 0) {
+                        push(0, 0);  // A_k l -> s1
+                        push(1, 1);  // A_k s -> s2
+                    } else if (fam == 1) {
+                        push(1, 0);  // A^_k s -> s1
+                    } else if (fam == 2) {
+                        push(0, 1);  // A~_k l -> s2
+                    } else {
+                        push(2, 1);  // tail slice * W_a -> s2
+                    }
+                }
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
+    auto make_list = [&](std::vector<HistTask>& tasks, std::vector<int>& rbs, TaskList& tl) -> int {
+        std::vector<int> order(tasks.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int a, int b) {
+            if (rbs[a] != rbs[b]) return rbs[a] < rbs[b];
+            if (tasks[a].k != tasks[b].k) return tasks[a].k < tasks[b].k;
+            return tasks[a].cb < tasks[b].cb;
+        });
+        std::vector<HistTask> sorted(tasks.size());
+        std::vector<int> srb(tasks.size());
+        for (size_t i = 0; i < order.size(); i++) {
+            sorted[i] = tasks[order[i]];
+            srb[i] = rbs[order[i]];
+        }
+        const size_t target_chunks = (size_t)4 * nsm;
+        const int ch = (int)std::max<size_t>(1, (sorted.size() + target_chunks - 1) / target_chunks);
+        std::vector<HistChunk> chunks;
+        std::vector<int> cptr(nrb + 1, 0);
+        size_t i = 0;
+        for (int rb = 0; rb < nrb; rb++) {
+            cptr[rb] = (int)chunks.size();
+            while (i < sorted.size() && srb[i] == rb) {
+                size_t j = i;
+                while (j < sorted.size() && srb[j] == rb && (int)(j - i) < ch) j++;
+                chunks.push_back(HistChunk{rb, (int)i, (int)(j - i)});
+                i = j;
+            }
+        }
+        cptr[nrb] = (int)chunks.size();
+        tl.ntasks = (int)sorted.size();
+        tl.nchunks = (int)chunks.size();
+        tl.tasks = (HistTask*)dalloc(h, sizeof(HistTask) * std::max<size_t>(1, sorted.size()));
+        tl.chunks = (HistChunk*)dalloc(h, sizeof(HistChunk) * std::max<size_t>(1, chunks.size()));
+        tl.chunk_ptr = (int*)dalloc(h, sizeof(int) * (nrb + 1));
+        if (!tl.tasks || !tl.chunks || !tl.chunk_ptr) return fail(h, MOT_EOOM, "device allocation (task list)");
+        if (!sorted.empty()) CK(cudaMemcpy(tl.tasks, sorted.data(), sizeof(HistTask) * sorted.size(), cudaMemcpyHostToDevice));
+        if (!chunks.empty()) CK(cudaMemcpy(tl.chunks, chunks.data(), sizeof(HistChunk) * chunks.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(tl.chunk_ptr, cptr.data(), sizeof(int) * (nrb + 1), cudaMemcpyHostToDevice));
+        return MOT_OK;
+    };
+    int st;
+    if ((st = make_list(th_hist, rb_hist, h->hist)) != MOT_OK) return st;
+    if ((st = make_list(th_lag0, rb_lag0, h->lag0)) != MOT_OK) return st;
+    h->d_tiles = (double*)dalloc(h, sizeof(double) * std::max<size_t>(1, tiles.size()));
+    if (!h->d_tiles) return fail(h, MOT_EOOM, "device allocation (history tiles)");
+    if (!tiles.empty()) CK(cudaMemcpy(h->d_tiles, tiles.data(), sizeof(double) * tiles.size(), cudaMemcpyHostToDevice));
+    return MOT_OK;
+}
+
+}  // namespace
+
+MOT_API int mot_load_operators(mot_handle* h, const mot_operators* ops) {
+    if (!h) return MOT_EINVAL;
+    if (h->loaded) return fail(h, MOT_ESTATE, "operators already loaded");
+    if (!ops || !ops->T0s || !ops->T0h || !ops->g_rowptr || !ops->g_col || !ops->g_val || !ops->rhs_x ||
+        !ops->rhs_wf || ops->nq <= 0)
+        return fail(h, MOT_EINVAL, "missing operator arrays");
+    CK(cudaSetDevice(h->dev));
+    const int ne = h->ne, np = h->npad;
+    // static operators, permuted and zero padded
+    std::vector<double> a((size_t)np * np, 0.0), b((size_t)np * np, 0.0);
+    for (int p = 0; p < ne; p++)
+        for (int q = 0; q < ne; q++) {
+            const size_t src = (size_t)h->perm[p] * ne + h->perm[q];
+            const double x = ops->T0s[src], y = ops->T0h[src];
+            if (!std::isfinite(x) || !std::isfinite(y)) return fail(h, MOT_EINVAL, "non-finite static operator");
+            a[(size_t)p * np + q] = x;
+            b[(size_t)p * np + q] = y;
+        }
+    h->d_T0s = (double*)dalloc(h, sizeof(double) * a.size());
+    h->d_T0h = (double*)dalloc(h, sizeof(double) * b.size());
+    if (!h->d_T0s || !h->d_T0h) return fail(h, MOT_EOOM, "device allocation (static operators)");
+    CK(cudaMemcpy(h->d_T0s, a.data(), sizeof(double) * a.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_T0h, b.data(), sizeof(double) * b.size(), cudaMemcpyHostToDevice));
+    // Gram matrix and transpose in the internal order
+    std::vector<std::tuple<int, int, double>> tg, tgt;
+    if (ops->g_rowptr[0] != 0) return fail(h, MOT_EINVAL, "G rowptr[0] != 0");
+    for (int m = 0; m < ne; m++)
+        for (int64_t e = ops->g_rowptr[m]; e < ops->g_rowptr[m + 1]; e++) {
+            const int n = ops->g_col[e];
+            const double v = ops->g_val[e];
+            if (n < 0 || n >= ne) return fail(h, MOT_EINVAL, "G column out of range");
+            if (!std::isfinite(v)) return fail(h, MOT_EINVAL, "non-finite G value");
+            tg.emplace_back(h->iperm[m], h->iperm[n], v);
+            tgt.emplace_back(h->iperm[n], h->iperm[m], v);
+        }
+    int st;
+    HostCsr G = csr_from_triplets(ne, ne, tg), Gt = csr_from_triplets(ne, ne, tgt);
+    if ((st = upload_csr(h, G, h->G)) != MOT_OK) return st;
+    if ((st = upload_csr(h, Gt, h->Gt)) != MOT_OK) return st;
+    // RHS quadrature table
+    h->nq = ops->nq;
+    std::vector<double> x((size_t)np * h->nq * 3, 0.0), wf((size_t)np * h->nq * 3, 0.0);
+    for (int p = 0; p < ne; p++) {
+        const size_t s = (size_t)h->perm[p] * h->nq * 3, d = (size_t)p * h->nq * 3;
+        for (int i = 0; i < h->nq * 3; i++) {
+            x[d + i] = ops->rhs_x[s + i];
+            wf[d + i] = ops->rhs_wf[s + i];
+            if (!std::isfinite(x[d + i]) || !std::isfinite(wf[d + i])) return fail(h, MOT_EINVAL, "non-finite RHS table");
+        }
+    }
+    h->d_rhs_x = (double*)dalloc(h, sizeof(double) * x.size());
+    h->d_rhs_wf = (double*)dalloc(h, sizeof(double) * wf.size());
+    if (!h->d_rhs_x || !h->d_rhs_wf) return fail(h, MOT_EOOM, "device allocation (RHS table)");
+    CK(cudaMemcpy(h->d_rhs_x, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_rhs_wf, wf.data(), sizeof(double) * wf.size(), cudaMemcpyHostToDevice));
+    if ((st = build_tiles(h, ops)) != MOT_OK) return st;
+    h->loaded = true;
+    return MOT_OK;
+}
+
+MOT_API int mot_set_frequencies(mot_handle* h, int n_freq, const double* omega) {
+    if (!h) return MOT_EINVAL;
+    if (h->step != 0 || h->B != 0) return fail(h, MOT_ESTATE, "set frequencies before the first step");
+    if (n_freq < 0 || (n_freq > 0 && !omega)) return fail(h, MOT_EINVAL, "bad frequency list");
+    CK(cudaSetDevice(h->dev));
+    if (h->d_omega) cudaFree(h->d_omega);
+    h->d_omega = nullptr;
+    h->nfreq = n_freq;
+    h->omega.assign(omega, omega + n_freq);
+    for (double w : h->omega)
+        if (!std::isfinite(w) || w < 0) return fail(h, MOT_EINVAL, "frequencies must be finite and >= 0");
+    if (n_freq > 0) {
+        h->d_omega = (double*)dalloc(h, sizeof(double) * n_freq);
+        if (!h->d_omega) return fail(h, MOT_EOOM, "device allocation (frequencies)");
+        CK(cudaMemcpy(h->d_omega, omega, sizeof(double) * n_freq, cudaMemcpyHostToDevice));
+    }
+    return MOT_OK;
+}
+
+MOT_API int mot_step(mot_handle* h, const mot_wave* waves, int B, double* w_out, void* stream) {
+    if (!h) return MOT_EINVAL;
+    if (!h->loaded) return fail(h, MOT_ESTATE, "mot_load_operators must come first");
+    if (B < 1 || B > MOT_MAX_B || !waves) return fail(h, MOT_EINVAL, "B must be in [1, 64] with B waves");
+    int st;
+    if ((st = check_waves(h, waves, B)) != MOT_OK) return st;
+    CK(cudaSetDevice(h->dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = ensure_state(h, B)) != MOT_OK) return st;
+    if ((st = upload_waves(h, waves, B, s)) != MOT_OK) return st;
+    st = do_step(h, s);
+    if (st != MOT_OK && st != MOT_ENOCONV) return st;
+    if (w_out) {
+        Work W = work_of(h);
+        if (is_device_ptr(w_out)) {
+            launch_pack_w(h, W.x, w_out, s);
+        } else {
+            launch_pack_w(h, W.x, W.tmp, s);
+            CK(cudaMemcpyAsync(w_out, W.tmp, sizeof(double) * (size_t)B * 2 * h->ne, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        CK(cudaGetLastError());
+    }
+    return st;
+}
+
+MOT_API int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, double* w_out, void* stream) {
+    if (!h) return MOT_EINVAL;
+    if (n_steps < 0) return fail(h, MOT_EINVAL, "n_steps < 0");
+    int worst = MOT_OK;
+    const bool dev = w_out && is_device_ptr(w_out);
+    for (int i = 0; i < n_steps; i++) {
+        double* dst = w_out ? w_out + (size_t)i * B * 2 * h->ne : nullptr;
+        (void)dev;
+        int st = mot_step(h, waves, B, dst, stream);
+        if (st == MOT_ENOCONV) worst = st;
+        else if (st != MOT_OK) return st;
+    }
+    return worst;
+}
+
+MOT_API int mot_get_currents(mot_handle* h, double* out) {
+    if (!h || !out) return MOT_EINVAL;
+    if (!h->d_cur || h->step == 0) return fail(h, MOT_ESTATE, "no step taken yet");
+    CK(cudaSetDevice(h->dev));
+    Work W = work_of(h);
+    const size_t n = (size_t)h->B * 4 * h->ne;
+    if (is_device_ptr(out)) {
+        launch_pack_cur(h, out, 0);
+    } else {
+        launch_pack_cur(h, W.Y4, 0);
+        CK(cudaMemcpy(out, W.Y4, sizeof(double) * n, cudaMemcpyDeviceToHost));
+    }
+    CK(cudaDeviceSynchronize());
+    return MOT_OK;
+}
+
+MOT_API int mot_fields(mot_handle* h, const mot_wave* waves, int n_dir, const double* dirs, double* E_out) {
+    if (!h || !E_out || (n_dir > 0 && !dirs)) return MOT_EINVAL;
+    if (!h->d_dft || h->nfreq == 0) return fail(h, MOT_ESTATE, "no Fourier sums: call mot_set_frequencies and step");
+    (void)waves;
+    CK(cudaSetDevice(h->dev));
+    double* dd = (double*)dalloc(h, sizeof(double) * 3 * std::max(1, n_dir));
+    double* de = (double*)dalloc(h, sizeof(double) * (size_t)h->B * h->nfreq * std::max(1, n_dir) * 6);
+    if (!dd || !de) return fail(h, MOT_EOOM, "device allocation (far field)");
+    CK(cudaMemcpy(dd, dirs, sizeof(double) * 3 * n_dir, cudaMemcpyHostToDevice));
+    launch_far_field(h, n_dir, dd, de, 0);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(E_out, de, sizeof(double) * (size_t)h->B * h->nfreq * n_dir * 6, cudaMemcpyDeviceToHost));
+    cudaFree(dd);
+    cudaFree(de);
+    h->device_bytes -= (int64_t)(sizeof(double) * 3 * std::max(1, n_dir) +
+                                 sizeof(double) * (size_t)h->B * h->nfreq * std::max(1, n_dir) * 6);
+    return MOT_OK;
+}
+
+MOT_API int mot_reset(mot_handle* h) {
+    if (!h) return MOT_EINVAL;
+    CK(cudaSetDevice(h->dev));
+    CK(cudaDeviceSynchronize());
+    free_state(h);
+    return MOT_OK;
+}
+
+namespace {
+struct StateHeader {
+    uint64_t magic;
+    int32_t ne, B, R, nfreq, npad, pad;
+    int64_t step;
+};
+const uint64_t kMagic = 0x4d4f545354415430ULL;
+}  // namespace
+
+MOT_API int mot_save_state(mot_handle* h, void* buf, size_t* size) {
+    if (!h || !size) return MOT_EINVAL;
+    if (!h->d_ring) return fail(h, MOT_ESTATE, "no march state");
+    const size_t bv = (size_t)h->npad * 2 * h->B;
+    const size_t ring = sizeof(double) * (size_t)h->R * 6 * bv;
+    const size_t cur = sizeof(double) * 4 * (size_t)h->npad * h->B;
+    const size_t dft = sizeof(double) * std::max(1, h->nfreq) * 4 * (size_t)h->npad * h->B * 2;
+    const size_t need = sizeof(StateHeader) + sizeof(double) * 10 * h->B + ring + cur + dft;
+    if (!buf) {
+        *size = need;
+        return MOT_OK;
+    }
+    if (*size < need) return fail(h, MOT_EINVAL, "state buffer too small");
+    CK(cudaSetDevice(h->dev));
+    CK(cudaDeviceSynchronize());
+    StateHeader hd{kMagic, h->ne, h->B, h->R, h->nfreq, h->npad, 0, h->step};
+    char* p = (char*)buf;
+    memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    memcpy(p, h->h_waves.data(), sizeof(double) * 10 * h->B);
+    p += sizeof(double) * 10 * h->B;
+    CK(cudaMemcpy(p, h->d_ring, ring, cudaMemcpyDeviceToHost));
+    p += ring;
+    CK(cudaMemcpy(p, h->d_cur, cur, cudaMemcpyDeviceToHost));
+    p += cur;
+    CK(cudaMemcpy(p, h->d_dft, dft, cudaMemcpyDeviceToHost));
+    *size = need;
+    return MOT_OK;
+}
+
+MOT_API int mot_load_state(mot_handle* h, const void* buf, size_t size) {
+    if (!h || !buf) return MOT_EINVAL;
+    if (!h->loaded) return fail(h, MOT_ESTATE, "load operators first");
+    StateHeader hd;
+    if (size < sizeof hd) return fail(h, MOT_EINVAL, "state buffer too small");
+    memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kMagic || hd.ne != h->ne || hd.R != h->R || hd.npad != h->npad || hd.nfreq != h->nfreq ||
+        hd.B < 1 || hd.B > MOT_MAX_B)
+        return fail(h, MOT_EINVAL, "state does not match this handle");
+    CK(cudaSetDevice(h->dev));
+    if (h->B != hd.B) {
+        free_state(h);
+    }
+    int st;
+    if ((st = ensure_state(h, hd.B)) != MOT_OK) return st;
+    const size_t bv = (size_t)h->npad * 2 * h->B;
+    const size_t ring = sizeof(double) * (size_t)h->R * 6 * bv;
+    const size_t cur = sizeof(double) * 4 * (size_t)h->npad * h->B;
+    const size_t dft = sizeof(double) * std::max(1, h->nfreq) * 4 * (size_t)h->npad * h->B * 2;
+    if (size < sizeof hd + sizeof(double) * 10 * h->B + ring + cur + dft)
+        return fail(h, MOT_EINVAL, "state buffer too small");
+    const char* p = (const char*)buf + sizeof hd;
+    h->h_waves.assign((const double*)p, (const double*)p + 10 * h->B);
+    CK(cudaMemcpy(h->d_waves, p, sizeof(double) * 10 * h->B, cudaMemcpyHostToDevice));
+    p += sizeof(double) * 10 * h->B;
+    CK(cudaMemcpy(h->d_ring, p, ring, cudaMemcpyHostToDevice));
+    p += ring;
+    CK(cudaMemcpy(h->d_cur, p, cur, cudaMemcpyHostToDevice));
+    p += cur;
+    CK(cudaMemcpy(h->d_dft, p, dft, cudaMemcpyHostToDevice));
+    h->step = hd.step;
+    return MOT_OK;
+}
+
+MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
+    if (!h || !info) return MOT_EINVAL;
+    info->ne = h->ne;
+    info->nv = h->nv;
+    info->nf = h->nf;
+    info->kmax = h->kmax;
+    info->K = h->K;
+    info->B = h->B;
+    info->step = h->step;
+    info->D = h->D;
+    info->tmax = h->tmax;
+    info->dt = h->dt;
+    info->last_gmres_iters = h->last_gmres_iters;
+    info->last_gmres_resid = h->last_gmres_resid;
+    info->last_cg_iters = h->last_cg_iters;
+    info->device_bytes = h->device_bytes;
+    info->gpu_launches = h->launches;
+    info->tile_fill = h->tile_fill;
+    info->tile_count = h->ntiles;
+    return MOT_OK;
+}
+
+MOT_API int mot_get_edges(mot_handle* h, int32_t* ev, int32_t* ef) {
+    if (!h || !ev || !ef) return MOT_EINVAL;
+    memcpy(ev, h->ev.data(), sizeof(int) * 2 * h->ne);
+    memcpy(ef, h->ef.data(), sizeof(int) * 2 * h->ne);
+    return MOT_OK;
+}
+
+MOT_API const char* mot_last_error(mot_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+MOT_API void mot_destroy(mot_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->dev);
+    cudaDeviceSynchronize();
+    free_state(h);
+    void* ptrs[] = {h->d_edge_faces, h->d_edge_verts, h->d_face_edges, h->d_face_sgn, h->d_iperm, h->d_cg_iters,
+                    h->vtx_edges.rowptr, h->vtx_edges.col, h->vtx_edges.val, h->Lf.rowptr, h->Lf.col, h->Lf.val,
+                    h->Lv.rowptr, h->Lv.col, h->Lv.val, h->G.rowptr, h->G.col, h->G.val, h->Gt.rowptr,
+                    h->Gt.col, h->Gt.val, h->d_T0s, h->d_T0h, h->d_rhs_x, h->d_rhs_wf, h->d_tiles,
+                    h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
+                    h->lag0.chunk_ptr, h->d_omega};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);
+    delete h;
+}

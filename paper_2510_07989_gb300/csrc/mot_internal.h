@@ -1,0 +1,168 @@
+// Internal declarations of the GB300 MOT library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mot.h"
+
+// Edge-block size of the block-sparse history tiles (rows and columns).
+#define MOT_TILE 32
+// Largest batch of plane waves per handle.
+#define MOT_MAX_B 64
+
+// One tile product of the history contraction:
+//   out[code.out] (TILE rows of row block rb, 2B columns)
+//     += tile (TILE x TILE) * panel(k, code.part, code.variant)[rows of column block cb]
+// part: 0 = loop coefficients l_{i-k}, 1 = star coefficients s_{i-k},
+//       2 = windowed sum W_k of l (constant tail of K~).
+// variant: 0 = [eta u, v / eta], 1 = [eta' u, v / eta'], 2 = [-v, u].
+struct HistTask {
+    int tile;
+    int cb;
+    int k;
+    int code;  // part | variant << 2 | out << 4
+};
+
+struct HistChunk {
+    int rb;
+    int first;
+    int count;
+};
+
+// Device CSR matrix.
+struct DCsr {
+    int n = 0, m = 0;
+    int64_t nnz = 0;
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    double* val = nullptr;
+};
+
+// Task list of one block-sparse contraction (history lags, or lag 0 inside Q_0).
+struct TaskList {
+    HistTask* tasks = nullptr;
+    HistChunk* chunks = nullptr;
+    int ntasks = 0;
+    int nchunks = 0;
+    int* chunk_ptr = nullptr;  // [nrb+1] chunk range of each row block (device)
+};
+
+struct mot_handle {
+    std::string err;
+    int dev = 0;
+    mot_options opt{};
+    // geometry and material
+    int nv = 0, nf = 0, ne = 0, npad = 0, nrb = 0;
+    double eps_r = 1, mu_r = 1, dt = 0, D = 0, tmax = 0, c = 1, cp = 1, eta = 1, etap = 1;
+    int kmax = 0, K = 0, R = 0;
+    std::vector<double> verts;
+    std::vector<int> tris, ev, ef, eo;
+    std::vector<int> perm, iperm;  // perm[p] = canonical edge at internal row p
+    bool loaded = false;
+
+    // topology on device (internal edge order)
+    int* d_edge_faces = nullptr;   // [ne][2] c+, c-
+    int* d_edge_verts = nullptr;   // [ne][2] v-, v+
+    int* d_face_edges = nullptr;   // [nf][3] internal edge ids
+    double* d_face_sgn = nullptr;  // [nf][3]
+    DCsr vtx_edges;                // vertex -> edges with sign (Lambda^T)
+    DCsr Lf, Lv;                   // Sigma^T Sigma (faces), Lambda^T Lambda (vertices)
+    DCsr G, Gt;                    // Gram matrix and its transpose (internal order)
+    double* d_T0s = nullptr;       // [npad][npad]
+    double* d_T0h = nullptr;
+    int nq = 0;
+    double* d_rhs_x = nullptr;     // [npad][nq][3]
+    double* d_rhs_wf = nullptr;
+
+    // block-sparse history
+    double* d_tiles = nullptr;
+    int64_t ntiles = 0;
+    double tile_fill = 0;
+    TaskList hist, lag0;
+    int max_tail_lag = 0;  // windows W_a needed for a in [1, max_tail_lag]
+
+    // march state (allocated at the first step for a batch size B)
+    int B = 0;
+    int64_t step = 0;
+    double* d_waves = nullptr;     // [B][10]
+    std::vector<double> h_waves;
+    double* d_ring = nullptr;      // [R][2 parts][3 variants][npad][2B]
+    double* d_win = nullptr;       // [max_tail_lag+1][npad][2B]
+    double* d_cur = nullptr;       // [4][npad][B] recovered currents of the last step
+    int nfreq = 0;
+    std::vector<double> omega;
+    double* d_omega = nullptr;
+    double* d_dft = nullptr;       // [nfreq][4][npad][B][2]
+    // work buffers
+    double* d_work = nullptr;
+    size_t work_bytes = 0;
+    double* d_partial = nullptr;   // [nchunks][2][TILE][2B]
+    size_t partial_bytes = 0;
+    // GMRES
+    int gm_m = 0;
+    double* d_V = nullptr;         // [(m+1)][npad][2B]
+    double* d_H = nullptr;         // [B][m+1][m]
+    double* d_g = nullptr;         // [B][m+1]
+    double* d_cs = nullptr;
+    double* d_sn = nullptr;
+    double* d_hcol = nullptr;      // [2][m+1][B] CGS2 coefficients
+    double* d_red = nullptr;       // reduction scratch
+    size_t red_bytes = 0;
+    double* d_resid = nullptr;     // [B]
+    double* h_resid = nullptr;     // pinned [B]
+    int* d_iperm = nullptr;        // [ne] canonical edge -> internal row
+    int* d_gm_active = nullptr;    // [B] GMRES system still iterating
+    int* d_gm_jend = nullptr;      // [B] Krylov dimension reached
+    double* d_gm_bnorm = nullptr;  // [B] |b|
+    int* d_cg_iters = nullptr;     // [0] max CG iterations, [1] non-converged solves
+    int* h_cg_iters = nullptr;     // pinned
+    int last_gmres_iters = 0;
+    double last_gmres_resid = 0;
+    int last_cg_iters = 0;
+    int64_t launches = 0;
+    int64_t device_bytes = 0;
+    cudaStream_t stream = nullptr;
+};
+
+// ---- kernels' host wrappers (implemented in the .cu files) ----
+namespace mot {
+
+// error helpers
+int fail(mot_handle* h, int code, const std::string& msg);
+int cuda_fail(mot_handle* h, cudaError_t e, const char* where);
+void* dalloc(mot_handle* h, size_t bytes);
+
+// history
+void launch_history(mot_handle* h, const TaskList& tl, const double* tiles, const double* ring, const double* win,
+                    const double* kry, int mode, long long step_i, double* out_s1, double* out_s2, cudaStream_t s);
+
+// block-vector helpers (rows npad, C columns)
+void launch_axpby(mot_handle* h, int n, double a, const double* x, double b, const double* y, double* z,
+                  cudaStream_t s);  // z = a x + b y, n doubles
+void launch_variants(mot_handle* h, const double* x, double* dst, double eta, double etap, cudaStream_t s);
+void launch_sigma_t(mot_handle* h, const double* x, int C, double* f, cudaStream_t s);   // faces <- edges
+void launch_sigma(mot_handle* h, const double* z, int C, double* x, cudaStream_t s);     // edges <- faces
+void launch_lambda_t(mot_handle* h, const double* x, int C, double* v, cudaStream_t s);  // vertices <- edges
+void launch_lambda(mot_handle* h, const double* z, int C, double* x, cudaStream_t s);    // edges <- vertices
+void launch_spmv(mot_handle* h, const DCsr& A, const double* x, int C, double* y, cudaStream_t s);
+int launch_cg(mot_handle* h, const DCsr& A, const DCsr* A2, const double* f, int C, double* z, double* work,
+              cudaStream_t s);  // returns max iterations or -1 on no convergence
+void launch_gemm(mot_handle* h, const double* A, const double* X, int C, double* Y, cudaStream_t s);
+void launch_rhs(mot_handle* h, long long i, double* rho1, double* rho2, cudaStream_t s);
+void launch_window_sums(mot_handle* h, long long i, cudaStream_t s);
+void launch_recover(mot_handle* h, long long i, cudaStream_t s);
+void launch_pack_w(mot_handle* h, const double* x, double* out, cudaStream_t s);  // internal -> [B][2][ne]
+
+// GMRES pieces
+void launch_gm_dots(mot_handle* h, const double* V, int nvec, const double* w, double* out, cudaStream_t s);
+void launch_gm_update(mot_handle* h, const double* V, int nvec, const double* coef, double* w, cudaStream_t s);
+void launch_gm_norm(mot_handle* h, const double* w, double* out, cudaStream_t s);
+void launch_gm_scale(mot_handle* h, const double* w, const double* nrm, double* v, cudaStream_t s);
+void launch_gm_arnoldi_finish(mot_handle* h, int j, const double* hcol, const double* nrm, cudaStream_t s);
+void launch_gm_init(mot_handle* h, const double* beta, int first_cycle, cudaStream_t s);
+void launch_gm_solve_update(mot_handle* h, double* y, double* x, cudaStream_t s);
+
+}  // namespace mot

@@ -1,0 +1,153 @@
+"""Parity of the CUDA MOT path (through the C ABI) with the dense FP64 oracle on
+the same seeded inputs. Tolerance 1e-10 relative to the run's peak for FP64
+(both sides are FP64; the GPU uses CG/Krylov solves to 1e-14 and GMRES to
+1e-12 on a Q_0 with cond < 30)."""
+import numpy as np
+import pytest
+
+from oracle import farfield as FF
+from oracle import mot as O
+from paper_2510_07989_gb300.inputs import meshes as MS
+from paper_2510_07989_gb300.inputs.assemble import assemble
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def M():
+    from paper_2510_07989_gb300.build import build
+    build()
+    from paper_2510_07989_gb300 import mot
+    mot.load_library()
+    return mot
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def test_canonical_edges_match_inputs(M, pr1_ops):
+    s = M.Solver(pr1_ops)
+    ev, ef = M.mot_get_edges(s.h)
+    assert np.array_equal(ev, pr1_ops.mesh.ev)
+    assert np.array_equal(ef, pr1_ops.mesh.ef)
+    info = s.info()
+    assert info["kmax"] == pr1_ops.kmax and info["K"] == pr1_ops.kmax + 1
+    assert abs(info["D"] - pr1_ops.D) < 1e-14 and abs(info["tmax"] - pr1_ops.tmax) < 1e-13
+
+
+def test_pr1_full_march(M, pr1_ops, pr1_system):
+    """PR1: icosphere L1, eps_r = 2, c dt = 0.2, 200 steps, 1 RHS."""
+    exc = MS.single_wave(pr1_ops.dt, 30, 60)
+    n = 200
+    W = M.Solver(pr1_ops).run(exc, n)[:, 0].reshape(n, -1)
+    ref = O.march(pr1_system, exc, n)
+    assert rel(W, ref) < TOL
+    ne = pr1_ops.ne
+    assert rel(W[:, :ne], ref[:, :ne]) < TOL and rel(W[:, ne:], ref[:, ne:]) < TOL
+
+
+@pytest.fixture(scope="module")
+def l2_case():
+    ops = assemble(MS.icosphere(2), 3.0, 1.0, 0.3)
+    return ops, O.build_system(ops), MS.fibonacci_batch(3, 0.3, w_steps=40, t0_steps=80)
+
+
+def test_ragged_batch_matches_oracle(M, l2_case):
+    """Icosphere L2 (480 edges: 15 tiles of 32), B = 3 Fibonacci plane waves."""
+    ops, S, exc = l2_case
+    n = 80
+    s = M.Solver(ops)
+    W = s.run(exc, n)
+    for b in range(3):
+        ref = O.march(S, exc, n, b=b)
+        assert rel(W[:, b].reshape(n, -1), ref) < TOL
+    assert s.info()["last_gmres_iters"] < 60
+
+
+def test_batch_equals_single_runs(M, l2_case):
+    ops, S, exc = l2_case
+    n = 30
+    Wb = M.Solver(ops).run(exc, n)
+    for b in range(3):
+        one = MS.Excitation(exc.A[b:b + 1], exc.p[b:b + 1], exc.k[b:b + 1], exc.w[b:b + 1], exc.t0[b:b + 1],
+                            exc.t_trunc[b:b + 1])
+        Ws = M.Solver(ops).run(one, n)
+        assert np.abs(Wb[:, b] - Ws[:, 0]).max() <= 1e-13 * np.abs(Ws).max()
+
+
+def test_currents_and_far_field(M, l2_case):
+    """Loop/star currents (Eq. (dis_jm)) and the far field from their Fourier
+    sums against the oracle's recovery and radiation integrals."""
+    ops, S, exc = l2_case
+    n = 120
+    omegas = np.array([0.5, 1.0])
+    s = M.Solver(ops)
+    M.mot_set_frequencies(s.h, omegas)
+    waves = M.mot_waves(exc)
+    cur = np.zeros((3, 4, ops.ne))
+    for _ in range(n):
+        M.mot_step(s.h, waves, 3)
+    M.mot_get_currents(s.h, cur)
+    dirs = np.array([[0.0, 0.0, 1.0], [0.6, 0.0, 0.8], [0.0, -1.0, 0.0]])
+    E = M.mot_fields(s.h, waves, dirs, len(omegas), 3)
+    for b in range(3):
+        ref = O.march(S, exc, n, b=b)
+        rc = O.recover(S, ref)
+        for j, key in enumerate(("j_loop", "j_star", "m_loop", "m_star")):
+            assert np.abs(cur[b, j] - rc[key][-1]).max() <= TOL * np.abs(rc[key]).max() + 1e-300
+        for f, w in enumerate(omegas):
+            dw = FF.dft_weights(w, ops.dt, n)
+            J = rc["j_loop"].T @ dw + rc["j_star"].T @ dw
+            Mm = rc["m_loop"].T @ dw + rc["m_star"].T @ dw
+            Er = FF.far_field(ops.rwg, J, Mm, w, 1.0, dirs) / FF.pulse_spectrum(exc, b, w)
+            assert np.abs(E[b, f] - Er).max() < 1e-9 * np.abs(Er).max()
+
+
+def test_state_save_load_resume(M, pr1_ops):
+    """N steps == N/2 steps + save + load into a fresh handle + N/2 steps (bitwise)."""
+    exc = MS.single_wave(pr1_ops.dt, 30, 60)
+    waves = M.mot_waves(exc)
+    a = M.Solver(pr1_ops)
+    Wa = a.run(exc, 60)
+    b = M.Solver(pr1_ops)
+    b.run(exc, 30)
+    blob = M.mot_save_state(b.h)
+    c = M.Solver(pr1_ops)
+    M.mot_load_state(c.h, blob)
+    out = np.zeros((1, 2, pr1_ops.ne))
+    for i in range(30, 60):
+        M.mot_step(c.h, waves, 1, out)
+        assert np.array_equal(out, Wa[i])
+
+
+def test_reset_restarts(M, pr1_ops):
+    exc = MS.single_wave(pr1_ops.dt, 30, 60)
+    s = M.Solver(pr1_ops)
+    W1 = s.run(exc, 20)
+    M.mot_reset(s.h)
+    W2 = s.run(exc, 20)
+    assert np.array_equal(W1, W2)
+
+
+def test_batch_size_change_rejected(M, pr1_ops):
+    s = M.Solver(pr1_ops)
+    s.run(MS.single_wave(pr1_ops.dt), 2)
+    with pytest.raises(M.MotError) as e:
+        s.run(MS.fibonacci_batch(2, pr1_ops.dt), 1)
+    assert e.value.code == M.MOT_EINVAL
+
+
+def test_device_output_buffer(M, pr1_ops):
+    torch = pytest.importorskip("torch")
+    exc = MS.single_wave(pr1_ops.dt, 30, 60)
+    waves = M.mot_waves(exc)
+    s = M.Solver(pr1_ops)
+    host = s.run(exc, 10)
+    M.mot_reset(s.h)
+    out = torch.zeros((1, 2, pr1_ops.ne), dtype=torch.float64, device="cuda")
+    for i in range(10):
+        M.mot_step(s.h, waves, 1, out, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), host[-1])
