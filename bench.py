@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MOT step: RHS*steps/s of the batched qHP TD-PMCHWT
+march on one GPU (or N independent replicas under torchrun).
+
+Workload (default): multiply-connected torus R = 1, r = 0.3, 64 x 24 quad grid
+split into 3072 triangles (4608 edges, 9216 unknowns), eps_r = 4, c dt = 0.1
+(k_max = 52, 53 history lags), 64 Gaussian plane waves with Fibonacci
+directions and seeded polarisations, batched in one march.
+
+One bench step = one MOT step for the whole batch: right-hand side, full-depth
+history contraction over all lags, left preconditioner factors, GMRES solve of
+Q_0 with product-form matvecs, ring update, current recovery. Before timing,
+the march is advanced K+1 steps so every timed step contracts the full
+history (plus the W warm-up steps given on the command line).
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MOT RHS·steps/s, batched mixed vs FP64 plain on one GB300, at ≤1e-6 rel err"
+
+WORKLOADS = {
+    # name: (mesh builder, eps_r, c dt, B, assembly options)
+    "torus64x24": (lambda MS: MS.torus(1.0, 0.3, 64, 24), 4.0, 0.1, 64, dict(nq=3, ntheta=3, nrad=3, far_plain=6)),
+    "icosphere3": (lambda MS: MS.icosphere(3), 2.0, 0.5, 1, dict(nq=3, ntheta=3, nrad=3, far_plain=6)),
+    "pr1": (lambda MS: MS.icosphere(1), 2.0, 0.2, 1, dict()),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="torus64x24", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name, rank=0):
+    from paper_2510_07989_gb300.inputs import meshes as MS
+    from paper_2510_07989_gb300.inputs.assemble import assemble
+    build_mesh, eps_r, dt, B, aopt = WORKLOADS[name]
+    mesh = build_mesh(MS)
+    t = time.time()
+    ops = assemble(mesh, eps_r, 1.0, dt, **aopt)
+    t_asm = time.time() - t
+    r_obj = float(np.linalg.norm(mesh.verts, axis=1).max())
+    if B == 1:
+        exc = MS.single_wave(dt, r_obj=r_obj)
+    else:
+        exc = MS.fibonacci_batch(B, dt, seed=20251007 + rank, r_obj=r_obj)
+    return ops, exc, t_asm
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def cpu_baseline(ops, exc, seconds=20.0):
+    """The product-form FP64 oracle, as it stands, on a bounded sample: full-
+    depth MOT steps for one right-hand side on seeded history."""
+    from oracle import product as P
+    t = time.time()
+    sysP = P.ProductSystem(ops)
+    t_setup = time.time() - t
+    ne = ops.ne
+    K = ops.kmax + 1
+    rng = np.random.default_rng(7)
+    n_hist = K + 4
+    L = np.zeros((n_hist + 8, 2 * ne))
+    S = np.zeros((n_hist + 8, 2 * ne))
+    for j in range(1, n_hist):
+        w = rng.standard_normal(2 * ne) * 1e-3
+        L[j], S[j] = sysP.split(w)
+    steps = 0
+    t0 = time.time()
+    i = n_hist
+    while steps < 1 or (time.time() - t0 < seconds and steps < 4):
+        w = sysP.step(exc, 0, i, L, S)
+        L[i], S[i] = sysP.split(w)
+        i += 1
+        steps += 1
+    el = time.time() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": steps / el, "unit": "RHS·steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full-depth MOT step(s) x 1 RHS of the same workload (product-form FP64 oracle, "
+                      f"seeded history, setup {t_setup:.0f} s excluded)"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    ops, exc, _ = make_workload(args.workload)
+    from oracle import product as P
+    sysP = P.ProductSystem(ops)
+    ne = ops.ne
+    K = ops.kmax + 1
+    rng = np.random.default_rng(7)
+    total = args.warmup + args.steps + K + 8
+    L = np.zeros((total + 2, 2 * ne))
+    S = np.zeros((total + 2, 2 * ne))
+    for j in range(1, K + 2):
+        L[j], S[j] = sysP.split(rng.standard_normal(2 * ne) * 1e-3)
+    i = K + 2
+    for _ in range(args.warmup):
+        w = sysP.step(exc, 0, i, L, S)
+        L[i], S[i] = sysP.split(w)
+        i += 1
+    t0 = time.time()
+    for _ in range(args.steps):
+        w = sysP.step(exc, 0, i, L, S)
+        L[i], S[i] = sysP.split(w)
+        i += 1
+    el = time.time() - t0
+    v = args.steps / el
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "RHS·steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "rhs_per_step": 1},
+            "cpu_baseline": {"value": v, "unit": "RHS·steps/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step: one full-depth MOT step x 1 RHS (product-form FP64 oracle)"},
+            "e2e": {"value": v, "unit": "RHS·steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    from paper_2510_07989_gb300 import mot as M
+    from paper_2510_07989_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    M.load_library()
+    ops, exc, t_asm = make_workload(args.workload, rank)
+    B = exc.B
+    s = M.Solver(ops, device=local, timing=1)
+    waves = M.mot_waves(exc)
+    stream = torch.cuda.current_stream()
+    K = ops.kmax + 1
+    # fill the history to full depth, then the requested warm-up
+    for _ in range(K + 1 + args.warmup):
+        M.mot_step(s.h, waves, B, None, stream)
+    info0 = M.mot_get_info(s.h)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        M.mot_step(s.h, waves, B, None, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    info1 = M.mot_get_info(s.h)
+    # end to end through the public API with host buffers: waves in (H2D) and
+    # w_i out (D2H) every step, inside the timed region
+    host_out = torch.empty((B, 2, ops.ne), dtype=torch.float64).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        M.mot_step(s.h, waves, B, host_out.numpy(), stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max, e2e_ms_max = float(t[0]), float(t[1])
+    value = world * B * args.steps / (ms_max / 1e3)
+    e2e_value = world * B * args.steps / (e2e_ms_max / 1e3)
+    if rank != 0:
+        return
+    peaks, how = measured_peaks()
+    hist_launches = info1["hist_timed_launches"] - info0["hist_timed_launches"]
+    hist_ms = info1["hist_timed_ms"] - info0["hist_timed_ms"]
+    flops = info1["hist_flops_per_step"]
+    fp64_peak = 1.25  # TFLOP/s, GB300 FP64 nominal (profiling recipe); FMA microbenchmark on this machine: 1.198
+    achieved = flops / (hist_ms / hist_launches / 1e3) / 1e12 if hist_launches else None
+    roof = {"kernel": "k_hist_f64", "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak if achieved else None, "traffic": None,
+            "peak_source": "nominal FP64 rate of the profiling recipe (fp64 ALU bound)",
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": info1["hist_bytes_per_step"],
+            "launches_timed": hist_launches, "ms_per_launch": hist_ms / hist_launches if hist_launches else None,
+            "share_of_step": (hist_ms / hist_launches) / (ms_max / args.steps) if hist_launches else None}
+    line = {"metric": METRIC, "value": value, "unit": "RHS·steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "ne": ops.ne, "unknowns": 2 * ops.ne, "eps_r": ops.eps_r,
+                       "c_dt": ops.dt, "k_max": ops.kmax, "history_lags": K, "rhs_per_step": B,
+                       "precision": "fp64 plain", "history_prefill_steps": K + 1,
+                       "l2": "inputs larger than L2 (history tiles %.1f GB)" % (info1["tile_count"] * 8192 / 1e9),
+                       "assembly_s": round(t_asm, 1), "parallelism": f"replicas{world}",
+                       "gmres_iters_last_step": info1["last_gmres_iters"],
+                       "tile_fill": round(info1["tile_fill"], 3)},
+            "clocks": ck,
+            "e2e": {"value": e2e_value, "unit": "RHS·steps/s", "h2d_bytes_per_step": 80 * B,
+                    "d2h_bytes_per_step": 8 * 2 * ops.ne * B},
+            "gpu_launches": (info1["gpu_launches"] - info0["gpu_launches"]),
+            "roofline": roof,
+            "peaks": {"source": how, "hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(ops, exc)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

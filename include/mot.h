@@ -61,6 +61,8 @@ typedef struct {
     int32_t gmres_maxit;   /* default 200 */
     double cg_tol;         /* relative residual of Laplacian / Gram solves, default 1e-14 */
     int32_t cg_maxit;      /* default 5000 */
+    int32_t timing;        /* 1: time every history-contraction launch with CUDA events
+                              on its stream (reported by mot_get_info); default 0 */
 } mot_options;
 
 /*
@@ -134,6 +136,15 @@ typedef struct {
     int64_t gpu_launches;       /* kernels launched by this handle so far */
     double tile_fill;           /* nonzero fraction of the stored history tiles */
     int64_t tile_count;         /* stored history tiles (all lags and families) */
+    /* algorithmic work of one full-depth history contraction (all lags live):
+       2 flops per stored nonzero per right-hand-side column it multiplies,
+       and 8 bytes per stored nonzero plus the coefficient ring it reads */
+    double hist_flops_per_step;
+    double hist_bytes_per_step;
+    /* with mot_options.timing: history-contraction launches (full depth, lags
+       1..K) timed so far and their summed CUDA-event duration */
+    int64_t hist_timed_launches;
+    double hist_timed_ms;
 } mot_info;
 
 /*

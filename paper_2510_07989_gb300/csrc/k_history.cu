@@ -121,8 +121,14 @@ void launch_history(mot_handle* h, const TaskList& tl, const double* tiles, cons
     const int C2 = 2 * h->B;
     if (tl.nchunks > 0) {
         size_t smem = sizeof(double) * (T * (T + 1) + T * C2);
+        const bool timed = h->opt.timing && mode == 0 && h->ev0 && step_i > h->K;
+        if (timed) cudaEventRecord(h->ev0, s);
         k_hist_f64<<<tl.nchunks, NT, smem, s>>>(tl.tasks, tl.chunks, tiles, ring, win, kry, mode, step_i, h->R,
                                                 h->npad, C2, h->d_partial);
+        if (timed) {
+            cudaEventRecord(h->ev1, s);
+            h->ev_pending = true;
+        }
         h->launches++;
     }
     k_hist_reduce<<<h->nrb, 256, 0, s>>>(tl.chunk_ptr, h->d_partial, h->nrb, C2, out_s1, out_s2);

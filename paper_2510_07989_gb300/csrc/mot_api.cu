@@ -369,11 +369,10 @@ int upload_waves(mot_handle* h, const mot_wave* waves, int B, cudaStream_t s) {
         double t[10] = {w.A, w.p[0], w.p[1], w.p[2], w.k[0], w.k[1], w.k[2], w.w, w.t0, w.t_trunc};
         memcpy(&v[10 * b], t, sizeof t);
     }
-    if (memcmp(v.data(), h->h_waves.data(), sizeof(double) * 10 * B) != 0) {
-        h->h_waves = v;
-        CK(cudaMemcpyAsync(h->d_waves, h->h_waves.data(), sizeof(double) * 10 * B, cudaMemcpyHostToDevice, s));
-        CK(cudaStreamSynchronize(s));
-    }
+    // the step's input is copied every step (B x 80 bytes)
+    h->h_waves = v;
+    CK(cudaMemcpyAsync(h->d_waves, h->h_waves.data(), sizeof(double) * 10 * B, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
     return MOT_OK;
 }
 
@@ -416,6 +415,13 @@ int do_step(mot_handle* h, cudaStream_t s) {
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_cg_iters, h->d_cg_iters, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (h->ev_pending) {
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        h->timed_ms += ms;
+        h->timed_launches++;
+        h->ev_pending = false;
+    }
     h->last_cg_iters = h->h_cg_iters[0];
     if (h->h_cg_iters[1] > 0) return fail(h, MOT_ENOCONV, "a projector or Gram CG solve reached its iteration limit");
     return st;
@@ -443,6 +449,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
         if (opt->gmres_maxit > 0) h->opt.gmres_maxit = opt->gmres_maxit;
         if (opt->cg_tol > 0) h->opt.cg_tol = opt->cg_tol;
         if (opt->cg_maxit > 0) h->opt.cg_maxit = opt->cg_maxit;
+        h->opt.timing = opt->timing;
     }
     auto bad = [&](const char* m) {
         h->err = m;
@@ -600,6 +607,10 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
     CK(cudaMemcpy(h->d_face_sgn, fs.data(), sizeof(double) * 3 * h->nf, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_iperm, h->iperm.data(), sizeof(int) * h->ne, cudaMemcpyHostToDevice));
     CK(cudaMallocHost(&h->h_cg_iters, sizeof(int) * 4));
+    if (h->opt.timing) {
+        CK(cudaEventCreate(&h->ev0));
+        CK(cudaEventCreate(&h->ev1));
+    }
     int st;
     if ((st = upload_csr(h, VE, h->vtx_edges)) != MOT_OK) return st;
     if ((st = upload_csr(h, LF, h->Lf)) != MOT_OK) return st;
@@ -708,8 +719,12 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
     for (int t = 0; t < nth; t++) th.emplace_back(fill, t, nth);
     for (auto& t : th) t.join();
     int64_t nz = 0;
-    for (double v : tiles) nz += v != 0.0;
+    std::vector<int> tnnz(nt, 0);
+    for (int64_t t = 0; t < nt; t++)
+        for (int e = 0; e < T * T; e++) tnnz[t] += tiles[(size_t)t * T * T + e] != 0.0;
+    for (int64_t t = 0; t < nt; t++) nz += tnnz[t];
     h->tile_fill = nt ? (double)nz / ((double)nt * T * T) : 0.0;
+    std::vector<char> used_hist(nt, 0);
     // task lists
     std::vector<HistTask> th_hist, th_lag0;
     std::vector<int> rb_hist, rb_lag0;
@@ -728,6 +743,11 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
                         } else {
                             th_hist.push_back(tk);
                             rb_hist.push_back(rb);
+                            h->hist_nnz_tasks += tnnz[t];
+                            if (!used_hist[t]) {
+                                used_hist[t] = 1;
+                                h->hist_nnz_unique += tnnz[t];
+                            }
                         }
                     };
                     if (fam == 0) {
@@ -1049,6 +1069,11 @@ MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
     info->gpu_launches = h->launches;
     info->tile_fill = h->tile_fill;
     info->tile_count = h->ntiles;
+    const double Bc = std::max(1, h->B);
+    info->hist_flops_per_step = 2.0 * h->hist_nnz_tasks * 2.0 * Bc;
+    info->hist_bytes_per_step = 8.0 * h->hist_nnz_unique + 8.0 * (double)h->K * 2.0 * 2.0 * h->ne * Bc;
+    info->hist_timed_launches = h->timed_launches;
+    info->hist_timed_ms = h->timed_ms;
     return MOT_OK;
 }
 
@@ -1075,5 +1100,7 @@ MOT_API void mot_destroy(mot_handle* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
     delete h;
 }

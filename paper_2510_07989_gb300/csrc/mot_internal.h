@@ -125,6 +125,14 @@ struct mot_handle {
     int64_t launches = 0;
     int64_t device_bytes = 0;
     cudaStream_t stream = nullptr;
+    // algorithmic work of a full-depth history contraction
+    double hist_nnz_tasks = 0;   // sum over history tasks of the tile's nonzeros
+    double hist_nnz_unique = 0;  // nonzeros of the stored tiles used by the history list
+    // CUDA-event timing of the history launches (mot_options.timing)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ev_pending = false;
+    int64_t timed_launches = 0;
+    double timed_ms = 0;
 };
 
 // ---- kernels' host wrappers (implemented in the .cu files) ----

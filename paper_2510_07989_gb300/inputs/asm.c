@@ -371,7 +371,7 @@ typedef struct {
     const int* EF;
     const int* EO;
     double c, dt, tmax;
-    int kmax, nq, nthreads;
+    int kmax, nq, nthreads, far_plain;
     Rule1D r1, r1far;
     Tri* tris;
     int* face_edges;      /* [nf][3] edge ids */
@@ -623,8 +623,8 @@ static void* td_worker(void* arg) {
                     sub3(x, TR->p[0], v0);
                     if (fabs(dot3(v0, TR->n)) < 1e-10 * TR->diam && fabs(dot3(TS->n, TR->n)) > 1.0 - 1e-12) coplanar = 1;
                 }
-                if (jlo == jhi && dc > 3.0 * TR->diam)
-                    nn = plain_nodes(x, TR, 7, th->nodes);
+                if ((jlo == jhi || C->far_plain) && dc > 3.0 * TR->diam)
+                    nn = plain_nodes(x, TR, C->far_plain ? C->far_plain : 7, th->nodes);
                 else if (dc > 3.0 * TR->diam)
                     nn = polar_nodes(x, TR, cdt, &C->r1far, th->nodes, th->cap);
                 else
@@ -838,7 +838,7 @@ static void merge_rows(TDCtx* C, TDResult* res) {
 
 void* asm_td_run(int nv, const double* V, int nf, const int* F, int ne, const int* EV, const int* EF,
                  const int* EO, double c, double dt, double tmax, int kmax, int nq, int ntheta, int nrad,
-                 int nthreads) {
+                 int nthreads, int far_plain) {
     TDCtx C;
     memset(&C, 0, sizeof C);
     C.nv = nv;
@@ -855,6 +855,7 @@ void* asm_td_run(int nv, const double* V, int nf, const int* F, int ne, const in
     C.kmax = kmax;
     C.nq = nq;
     C.nthreads = nthreads < 1 ? 1 : nthreads;
+    C.far_plain = far_plain;
     C.r1.nt = ntheta;
     C.r1.nr = nrad;
     gauss_legendre01(ntheta, C.r1.gt_x, C.r1.gt_w);

@@ -54,7 +54,7 @@ def _load():
         _lib.asm_td_run.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                    ctypes.c_int, ctypes.c_int]
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int]
         _lib.asm_td_sizes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         _lib.asm_td_copy.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 8
         _lib.asm_td_free.argtypes = [ctypes.c_void_p]
@@ -138,7 +138,7 @@ def k_max_of(tmax: float, dt: float) -> int:
 
 
 def _run_medium(mesh: Mesh, c: float, dt: float, tmax: float, kmax: int, nq: int, ntheta: int, nrad: int,
-                nthreads: int) -> dict:
+                nthreads: int, far_plain: int = 0) -> dict:
     lib = _load()
     V = np.ascontiguousarray(mesh.verts, dtype=np.float64)
     F = np.ascontiguousarray(mesh.tris, dtype=np.int32)
@@ -146,7 +146,7 @@ def _run_medium(mesh: Mesh, c: float, dt: float, tmax: float, kmax: int, nq: int
     EF = np.ascontiguousarray(mesh.ef, dtype=np.int32)
     EO = np.ascontiguousarray(mesh.eo, dtype=np.int32)
     h = lib.asm_td_run(mesh.nv, _ptr(V), mesh.nf, _ptr(F), mesh.ne, _ptr(EV), _ptr(EF), _ptr(EO),
-                       c, dt, tmax, kmax, nq, ntheta, nrad, nthreads)
+                       c, dt, tmax, kmax, nq, ntheta, nrad, nthreads, far_plain)
     out = {}
     try:
         for kind, name in enumerate(KINDS):
@@ -208,11 +208,13 @@ def _static(mesh: Mesh, dual: DualBasis, D: float, nq: int, ntheta: int, nrad: i
 
 def assemble(mesh: Mesh, eps_r: float, mu_r: float, dt: float, *, nq: int = 7, ntheta: int = 4, nrad: int = 4,
              nq_static: int = 3, nthreads: int | None = None, with_bc_table: bool = False,
-             kmax: int | None = None) -> Operators:
+             kmax: int | None = None, far_plain: int = 0) -> Operators:
     """Assemble every input of the MOT step for one scatterer (c = 1 outside).
 
     nq is the outer (test) triangle rule; ntheta / nrad the Gauss orders of the
-    polar inner integration per smooth piece."""
+    polar inner integration per smooth piece. far_plain > 0 replaces the
+    shell-split polar rule by a plain far_plain-point triangle rule for source
+    triangles farther than three diameters (fast, less accurate assembly)."""
     if nthreads is None:
         nthreads = os.cpu_count() or 1
     c = 1.0
@@ -225,7 +227,7 @@ def assemble(mesh: Mesh, eps_r: float, mu_r: float, dt: float, *, nq: int = 7, n
         kmax = k_max_of(tmax, dt)
     mats = {}
     for suffix, cc in (("", c), ("p", cp)):
-        res = _run_medium(mesh, cc, dt, tmax, kmax, nq, ntheta, nrad, nthreads)
+        res = _run_medium(mesh, cc, dt, tmax, kmax, nq, ntheta, nrad, nthreads, far_plain)
         for name, m in res.items():
             mats[name + suffix] = m
     dual = dual_basis(mesh)
@@ -236,5 +238,5 @@ def assemble(mesh: Mesh, eps_r: float, mu_r: float, dt: float, *, nq: int = 7, n
     ops = Operators(mesh=mesh, eps_r=eps_r, mu_r=mu_r, dt=dt, c=c, cp=cp, eta=eta, etap=etap, D=D, tmax=tmax,
                     kmax=kmax, mats=mats, T0s=T0s, T0h=T0h, G=G, rwg=rwg_table(mesh, 7), dual=dual,
                     bc=bc_table(dual) if with_bc_table else None,
-                    meta=dict(nq=nq, ntheta=ntheta, nrad=nrad, nq_static=nq_static))
+                    meta=dict(nq=nq, ntheta=ntheta, nrad=nrad, nq_static=nq_static, far_plain=far_plain))
     return ops

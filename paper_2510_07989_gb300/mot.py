@@ -32,7 +32,8 @@ class mot_mesh(ctypes.Structure):
 
 class mot_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("device", ctypes.c_int32), ("gmres_tol", ctypes.c_double),
-                ("gmres_maxit", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int32)]
+                ("gmres_maxit", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int32),
+                ("timing", ctypes.c_int32)]
 
 
 class mot_lagmat(ctypes.Structure):
@@ -58,7 +59,9 @@ class mot_info(ctypes.Structure):
                 ("tmax", ctypes.c_double), ("dt", ctypes.c_double), ("last_gmres_iters", ctypes.c_int32),
                 ("last_gmres_resid", ctypes.c_double), ("last_cg_iters", ctypes.c_int32),
                 ("device_bytes", ctypes.c_int64), ("gpu_launches", ctypes.c_int64), ("tile_fill", ctypes.c_double),
-                ("tile_count", ctypes.c_int64)]
+                ("tile_count", ctypes.c_int64), ("hist_flops_per_step", ctypes.c_double),
+                ("hist_bytes_per_step", ctypes.c_double), ("hist_timed_launches", ctypes.c_int64),
+                ("hist_timed_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -162,12 +165,12 @@ class Handle:
 
 
 def mot_create(verts, tris, eps_r, mu_r, dt, K, precision=MOT_PREC_FP64, device=0, gmres_tol=1e-12,
-               gmres_maxit=200, cg_tol=1e-14, cg_maxit=5000) -> Handle:
+               gmres_maxit=200, cg_tol=1e-14, cg_maxit=5000, timing=0) -> Handle:
     lib = load_library()
     V = _c(verts, np.float64)
     Tr = _c(tris, np.int32)
     mesh = mot_mesh(V.shape[0], V.ctypes.data, Tr.shape[0], Tr.ctypes.data)
-    opt = mot_options(precision, device, gmres_tol, gmres_maxit, cg_tol, cg_maxit)
+    opt = mot_options(precision, device, gmres_tol, gmres_maxit, cg_tol, cg_maxit, int(timing))
     out = ctypes.c_void_p()
     code = lib.mot_create(ctypes.byref(mesh), float(eps_r), float(mu_r), float(dt), int(K), ctypes.byref(opt),
                           ctypes.byref(out))
