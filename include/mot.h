@@ -204,6 +204,24 @@ int mot_get_currents(mot_handle* h, double* out);
  */
 int mot_fields(mot_handle* h, const mot_wave* waves, int n_dir, const double* dirs, double* E_out);
 
+/*
+ * mot_fields_noalloc: the same far field as mot_fields, computed without
+ * allocating device memory during the call. The paper has no counterpart; it
+ * exists for callers that may not call cudaMalloc / cudaFree at that point,
+ * e.g. an application whose memory pool owns all device memory after start-up,
+ * or a latency-critical loop in which allocation would synchronise the device.
+ * mot_fields allocates staging buffers for the directions and the result on
+ * every call; this variant stages them in one fixed device array of 262144
+ * doubles (2 MiB) built into the library, which every GPU that loads the
+ * library keeps until the process exits.
+ *   Limit: 3*n_dir + 6*B*n_freq*n_dir <= 262144, else MOT_EINVAL with a message.
+ *   The first call on a device looks up the array's device address (once per
+ *   device); make that first call before any stream capture.
+ *   All calls share the array: calls whose GPU work overlaps race on it, so the
+ *   caller must serialise them. Arguments and E_out layout as for mot_fields.
+ */
+int mot_fields_noalloc(mot_handle* h, const mot_wave* waves, int n_dir, const double* dirs, double* E_out);
+
 /* Restart the march at step 0 (operators kept). */
 int mot_reset(mot_handle* h);
 

@@ -12,6 +12,8 @@
 #define MOT_TILE 32
 // Largest batch of plane waves per handle.
 #define MOT_MAX_B 64
+// Size (doubles) of the fixed device array used by mot_fields_noalloc.
+#define MOT_NOALLOC_FIELD_DOUBLES 262144
 
 // One tile product of the history contraction:
 //   out[code.out] (TILE rows of row block rb, 2B columns)

@@ -68,8 +68,8 @@ class mot_info(ctypes.Structure):
 
 
 EXPORTED = ["mot_create", "mot_load_operators", "mot_set_frequencies", "mot_step", "mot_run", "mot_get_currents",
-            "mot_fields", "mot_reset", "mot_save_state", "mot_load_state", "mot_get_info", "mot_get_edges",
-            "mot_last_error", "mot_destroy"]
+            "mot_fields", "mot_fields_noalloc", "mot_reset", "mot_save_state", "mot_load_state", "mot_get_info",
+            "mot_get_edges", "mot_last_error", "mot_destroy"]
 
 _lib = None
 
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.mot_run.argtypes = [vp, i32, vp, i32, vp, vp]
     lib.mot_get_currents.argtypes = [vp, vp]
     lib.mot_fields.argtypes = [vp, vp, i32, vp, vp]
+    lib.mot_fields_noalloc.argtypes = [vp, vp, i32, vp, vp]
     lib.mot_reset.argtypes = [vp]
     lib.mot_save_state.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.mot_load_state.argtypes = [vp, vp, ctypes.c_size_t]
@@ -239,6 +240,18 @@ def mot_fields(h: Handle, waves, dirs, n_freq: int, B: int) -> np.ndarray:
     out = np.zeros((B, n_freq, d.shape[0], 3, 2))
     _check(h.ptr, load_library().mot_fields(h.ptr, ctypes.cast(waves, ctypes.c_void_p), d.shape[0], d.ctypes.data,
                                             out.ctypes.data))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def mot_fields_noalloc(h: Handle, waves, dirs, n_freq: int, B: int) -> np.ndarray:
+    """Same result as mot_fields without any device allocation in the call: the
+    library stages directions and result in a fixed 2 MiB device array (for
+    callers that must not call cudaMalloc at this point). Calls must not
+    overlap on the GPU; 3*n_dir + 6*B*n_freq*n_dir <= 262144."""
+    d = _c(dirs, np.float64).reshape(-1, 3)
+    out = np.zeros((B, n_freq, d.shape[0], 3, 2))
+    _check(h.ptr, load_library().mot_fields_noalloc(h.ptr, ctypes.cast(waves, ctypes.c_void_p), d.shape[0],
+                                                    d.ctypes.data, out.ctypes.data))
     return out[..., 0] + 1j * out[..., 1]
 
 
