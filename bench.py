@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="torus64x24", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     return ap.parse_args()
 
 
@@ -220,7 +221,10 @@ def run_ours(args):
     M.load_library()
     ops, exc, t_asm = make_workload(args.workload, rank)
     B = exc.B
-    s = M.Solver(ops, device=local, timing=1)
+    prec = M.MOT_PREC_MIXED if args.precision == "mixed" else M.MOT_PREC_FP64
+    t = time.time()
+    s = M.Solver(ops, device=local, timing=1, precision=prec)
+    t_load = time.time() - t
     waves = M.mot_waves(exc)
     stream = torch.cuda.current_stream()
     K = ops.kmax + 1
@@ -271,20 +275,26 @@ def run_ours(args):
     hist_launches = info1["hist_timed_launches"] - info0["hist_timed_launches"]
     hist_ms = info1["hist_timed_ms"] - info0["hist_timed_ms"]
     flops = info1["hist_flops_per_step"]
-    fp64_peak = 1.25  # TFLOP/s, GB300 FP64 nominal (profiling recipe); FMA microbenchmark on this machine: 1.198
+    if args.precision == "mixed":
+        peak, kname = 70.0, "k_hist_f32"  # FP32 FMA microbenchmark on this pool: 69.8-70.0 TFLOP/s
+        psrc = "FP32 CUDA-core FMA rate measured on this pool (152 SMs x 128 lanes x 2 x clock)"
+    else:
+        peak, kname = 1.25, "k_hist_f64"  # GB300 FP64 nominal; FMA microbenchmark on this pool: 1.198
+        psrc = "nominal FP64 rate of the profiling recipe (fp64 ALU bound)"
     achieved = flops / (hist_ms / hist_launches / 1e3) / 1e12 if hist_launches else None
-    roof = {"kernel": "k_hist_f64", "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak if achieved else None, "traffic": None,
-            "peak_source": "nominal FP64 rate of the profiling recipe (fp64 ALU bound)",
+    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_source": psrc,
             "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": info1["hist_bytes_per_step"],
             "launches_timed": hist_launches, "ms_per_launch": hist_ms / hist_launches if hist_launches else None,
             "share_of_step": (hist_ms / hist_launches) / (ms_max / args.steps) if hist_launches else None}
     line = {"metric": METRIC, "value": value, "unit": "RHS·steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "ne": ops.ne, "unknowns": 2 * ops.ne, "eps_r": ops.eps_r,
                        "c_dt": ops.dt, "k_max": ops.kmax, "history_lags": K, "rhs_per_step": B,
-                       "precision": "fp64 plain", "history_prefill_steps": K + 1,
+                       "precision": "mixed (FP32 history tiles, dense FP32 Q_0 and left factors, FP64 sums, FP64 CG projector)" if args.precision == "mixed" else "fp64 plain",
+                       "history_prefill_steps": K + 1, "load_s": round(t_load, 1),
                        "l2": "inputs larger than L2 (history tiles %.1f GB)" % (info1["tile_count"] * 8192 / 1e9),
                        "assembly_s": round(t_asm, 1), "parallelism": f"replicas{world}",
                        "gmres_iters_last_step": info1["last_gmres_iters"],

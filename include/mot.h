@@ -63,7 +63,15 @@ typedef struct {
     int32_t cg_maxit;      /* default 5000 */
     int32_t timing;        /* 1: time every history-contraction launch with CUDA events
                               on its stream (reported by mot_get_info); default 0 */
+    int32_t mixed_flags;   /* MOT_PREC_MIXED only; 0 = default (MOT_MIX_DEFAULT). Bits:
+                              MOT_MIX_HIST32: FP32 history tiles and panels
+                              MOT_MIX_LF32:   FP32 dense left factor [M1 | M2]
+                              MOT_MIX_Q032:   FP32 dense Q_0 in the GMRES iterations
+                              MOT_MIX_REFINE: FP64 iterative refinement of the Q_0 solve */
 } mot_options;
+
+enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8,
+       MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE };
 
 /*
  * Lag-window sparse matrix (one family / medium of Section V-B):

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(NT) k_hist_f64(const HistTask* __restrict__ ta
                                                  const double* __restrict__ tiles, const double* __restrict__ ring,
                                                  const double* __restrict__ win, const double* __restrict__ kry,
                                                  int mode, long long step_i, int R, int npad, int C2,
-                                                 double* __restrict__ partial) {
+                                                 const int* __restrict__ colidx, double* __restrict__ partial) {
     extern __shared__ double sm[];
     double* st = sm;                  // T x (T + 1)
     double* sp = st + T * (T + 1);    // T x C2
@@ -50,12 +50,15 @@ __global__ void __launch_bounds__(NT) k_hist_f64(const HistTask* __restrict__ ta
         const HistTask tk = tasks[t];
         const int part = tk.code & 3, variant = (tk.code >> 2) & 3, out = (tk.code >> 4) & 1;
         if (mode == 0 && step_i - tk.k < 1) continue;  // history before step 1 is zero
-        const double* pan = panel_ptr(mode, ring, win, kry, step_i, R, npad, C2, tk.k, part, variant) +
-                            (size_t)tk.cb * T * C2;
+        const double* pan = panel_ptr(mode, ring, win, kry, step_i, R, npad, C2, tk.k, part, variant);
+        const int* cols = colidx + (size_t)ch.rb * npad + (size_t)tk.cb * T;  // distance-sorted columns
         const double* tl = tiles + (size_t)tk.tile * T * T;
         __syncthreads();
         for (int e = tid; e < T * T; e += NT) st[(e / T) * (T + 1) + (e % T)] = tl[e];
-        for (int e = tid; e < T * C2; e += NT) sp[e] = pan[e];
+        for (int e = tid; e < T * C2; e += NT) {
+            const int r = e / C2;
+            sp[e] = pan[(size_t)cols[r] * C2 + (e - r * C2)];
+        }
         __syncthreads();
         if (out == 0) {
 #pragma unroll
@@ -124,7 +127,7 @@ void launch_history(mot_handle* h, const TaskList& tl, const double* tiles, cons
         const bool timed = h->opt.timing && mode == 0 && h->ev0 && step_i > h->K;
         if (timed) cudaEventRecord(h->ev0, s);
         k_hist_f64<<<tl.nchunks, NT, smem, s>>>(tl.tasks, tl.chunks, tiles, ring, win, kry, mode, step_i, h->R,
-                                                h->npad, C2, h->d_partial);
+                                                h->npad, C2, h->d_colidx, h->d_partial);
         if (timed) {
             cudaEventRecord(h->ev1, s);
             h->ev_pending = true;

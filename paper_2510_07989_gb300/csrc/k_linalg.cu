@@ -198,8 +198,9 @@ __global__ void __launch_bounds__(1024) k_cg(int N, int C, CsrV A, CsrV A2, cons
 // ----------------------------------------------------------------- dense GEMM
 // Y[n][C] = A[n][n] X[n][C] (n = npad, multiple of 32), FP64.
 constexpr int GB_M = 64, GB_K = 32, GB_N = 32;
-__global__ void __launch_bounds__(256) k_gemm(int n, int C, const double* __restrict__ A,
+__global__ void __launch_bounds__(256) k_gemm(int n, int K, int C, const double* __restrict__ A,
                                               const double* __restrict__ X, double* __restrict__ Y) {
+    // rows n, contraction K (multiple of GB_K), A row-major with lda = K
     __shared__ double sa[GB_M][GB_K + 1];
     __shared__ double sx[GB_K][GB_N];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -207,10 +208,10 @@ __global__ void __launch_bounds__(256) k_gemm(int n, int C, const double* __rest
     double acc[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) acc[i] = 0.0;
-    for (int k0 = 0; k0 < n; k0 += GB_K) {
+    for (int k0 = 0; k0 < K; k0 += GB_K) {
         for (int e = threadIdx.x; e < GB_M * GB_K; e += 256) {
             const int r = e / GB_K, k = e - r * GB_K;
-            sa[r][k] = (row0 + r < n) ? A[(size_t)(row0 + r) * n + k0 + k] : 0.0;
+            sa[r][k] = (row0 + r < n) ? A[(size_t)(row0 + r) * K + k0 + k] : 0.0;
         }
         for (int e = threadIdx.x; e < GB_K * GB_N; e += 256) {
             const int k = e / GB_N, cc = e - k * GB_N;
@@ -230,6 +231,32 @@ __global__ void __launch_bounds__(256) k_gemm(int n, int C, const double* __rest
         for (int i = 0; i < 8; i++) {
             const int r = row0 + ty + 8 * i;
             if (r < n) Y[(size_t)r * C + col0 + tx] = acc[i];
+        }
+    }
+}
+
+// Y[n][C] = A[n][n] X[n][C] for C <= 8: one warp per row, lanes over the
+// contraction index (coalesced rows of A), warp-shuffle reduction.
+template <int CC>
+__global__ void __launch_bounds__(256) k_gemv_small(int n, int K, const double* __restrict__ A,
+                                                    const double* __restrict__ X, double* __restrict__ Y) {
+    const int lane = threadIdx.x & 31;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n; row += (gridDim.x * blockDim.x) >> 5) {
+        double acc[CC];
+#pragma unroll
+        for (int c = 0; c < CC; c++) acc[c] = 0.0;
+        const double* a = A + (size_t)row * K;
+        for (int k = lane; k < K; k += 32) {
+            const double av = a[k];
+#pragma unroll
+            for (int c = 0; c < CC; c++) acc[c] = fma(av, X[(size_t)k * CC + c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < CC; c++) {
+            double v = acc[c];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) Y[(size_t)row * CC + c] = v;
         }
     }
 }
@@ -667,10 +694,29 @@ int launch_cg(mot_handle* h, const DCsr& A, const DCsr* A2, const double* f, int
     return 0;
 }
 
-void launch_gemm(mot_handle* h, const double* A, const double* X, int C, double* Y, cudaStream_t s) {
-    dim3 grid((h->npad + GB_M - 1) / GB_M, (C + GB_N - 1) / GB_N);
-    k_gemm<<<grid, 256, 0, s>>>(h->npad, C, A, X, Y);
+void launch_gemm_rect(mot_handle* h, int M, int K, const double* A, const double* X, int C, double* Y,
+                      cudaStream_t s) {
+    if (C <= 8) {
+        const int g = grid_for((long long)M * 32);
+        switch (C) {
+            case 1: k_gemv_small<1><<<g, 256, 0, s>>>(M, K, A, X, Y); break;
+            case 2: k_gemv_small<2><<<g, 256, 0, s>>>(M, K, A, X, Y); break;
+            case 4: k_gemv_small<4><<<g, 256, 0, s>>>(M, K, A, X, Y); break;
+            case 6: k_gemv_small<6><<<g, 256, 0, s>>>(M, K, A, X, Y); break;
+            case 8: k_gemv_small<8><<<g, 256, 0, s>>>(M, K, A, X, Y); break;
+            default: goto general;
+        }
+        h->launches++;
+        return;
+    }
+general:
+    dim3 grid((M + GB_M - 1) / GB_M, (C + GB_N - 1) / GB_N);
+    k_gemm<<<grid, 256, 0, s>>>(M, K, C, A, X, Y);
     h->launches++;
+}
+
+void launch_gemm(mot_handle* h, const double* A, const double* X, int C, double* Y, cudaStream_t s) {
+    launch_gemm_rect(h, h->npad, h->npad, A, X, C, Y, s);
 }
 
 void launch_rhs(mot_handle* h, long long i, double* rho1, double* rho2, cudaStream_t s) {
@@ -736,7 +782,7 @@ void launch_gm_init(mot_handle* h, const double* beta, int first_cycle, cudaStre
 
 void launch_gm_arnoldi_finish(mot_handle* h, int j, const double* hcol, const double* nrm, cudaStream_t s) {
     k_gm_arnoldi<<<1, 64, 0, s>>>(h->B, h->gm_m, j, hcol, nrm, h->d_H, h->d_g, h->d_cs, h->d_sn, h->d_gm_active,
-                                  h->d_gm_jend, h->d_gm_bnorm, h->opt.gmres_tol, h->d_resid);
+                                  h->d_gm_jend, h->d_gm_bnorm, h->gm_tol, h->d_resid);
     h->launches++;
 }
 

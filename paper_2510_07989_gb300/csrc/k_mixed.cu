@@ -1,0 +1,297 @@
+// Kernels of the mixed-precision MOT path: FP32 history tiles and coefficient
+// panels with FP32 products summed in FP64 across tiles, a dense FP32 x FP32
+// -> FP64 GEMM for the precomputed Q_0 and left factors, and the load-time
+// helpers that assemble those dense matrices column by column from the FP64
+// product form.
+#include "mot_internal.h"
+
+namespace {
+
+constexpr int T = MOT_TILE;
+constexpr int NT = 256;
+constexpr int MAXO = T * 2 * MOT_MAX_B / NT;  // 16 outputs per thread per target
+constexpr int FLUSH = 4;                     // tiles summed in FP32 before an FP64 flush
+
+__device__ __forceinline__ const float* panel_ptr32(int mode, const float* ring, const float* win, const float* kry,
+                                                    long long step_i, int R, int npad, int C2, int k, int part,
+                                                    int variant) {
+    const size_t ps = (size_t)npad * C2;
+    if (mode == 1) return kry + ((size_t)part * 3 + variant) * ps;
+    if (part == 2) return win + (size_t)k * ps;
+    const int slot = (int)((step_i - k) % R);
+    return ring + (((size_t)slot * 2 + part) * 3 + variant) * ps;
+}
+
+__global__ void __launch_bounds__(NT) k_hist_f32(const HistTask* __restrict__ tasks,
+                                                 const HistChunk* __restrict__ chunks,
+                                                 const float* __restrict__ tiles, const float* __restrict__ ring,
+                                                 const float* __restrict__ win, const float* __restrict__ kry,
+                                                 int mode, long long step_i, int R, int npad, int C2,
+                                                 const int* __restrict__ colidx, double* __restrict__ partial) {
+    __shared__ float st[T * (T + 1)];
+    __shared__ float sp[T * 2 * MOT_MAX_B];
+    const HistChunk ch = chunks[blockIdx.x];
+    const int nout = T * C2;
+    const int tid = threadIdx.x;
+    float a0[MAXO], a1[MAXO];
+    double d0[MAXO], d1[MAXO];
+#pragma unroll
+    for (int j = 0; j < MAXO; j++) {
+        a0[j] = a1[j] = 0.f;
+        d0[j] = d1[j] = 0.0;
+    }
+    int pending = 0;
+    for (int t = ch.first; t < ch.first + ch.count; t++) {
+        const HistTask tk = tasks[t];
+        const int part = tk.code & 3, variant = (tk.code >> 2) & 3, out = (tk.code >> 4) & 1;
+        if (mode == 0 && step_i - tk.k < 1) continue;
+        const float* pan = panel_ptr32(mode, ring, win, kry, step_i, R, npad, C2, tk.k, part, variant);
+        const int* cols = colidx + (size_t)ch.rb * npad + (size_t)tk.cb * T;
+        const float* tl = tiles + (size_t)tk.tile * T * T;
+        __syncthreads();
+        for (int e = tid; e < T * T; e += NT) st[(e / T) * (T + 1) + (e % T)] = tl[e];
+        for (int e = tid; e < T * C2; e += NT) {
+            const int r = e / C2;
+            sp[e] = pan[(size_t)cols[r] * C2 + (e - r * C2)];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < MAXO; j++) {
+            const int o = tid + j * NT;
+            if (o < nout) {
+                const int r = o / C2, c = o - r * C2;
+                float s = 0.f;
+#pragma unroll 8
+                for (int n = 0; n < T; n++) s = fmaf(st[r * (T + 1) + n], sp[n * C2 + c], s);
+                if (out == 0)
+                    a0[j] += s;
+                else
+                    a1[j] += s;
+            }
+        }
+        if (++pending == FLUSH) {
+            pending = 0;
+#pragma unroll
+            for (int j = 0; j < MAXO; j++) {
+                d0[j] += (double)a0[j];
+                d1[j] += (double)a1[j];
+                a0[j] = a1[j] = 0.f;
+            }
+        }
+    }
+    double* dst = partial + (size_t)blockIdx.x * 2 * nout;
+#pragma unroll
+    for (int j = 0; j < MAXO; j++) {
+        const int o = tid + j * NT;
+        if (o < nout) {
+            dst[o] = d0[j] + (double)a0[j];
+            dst[nout + o] = d1[j] + (double)a1[j];
+        }
+    }
+}
+
+__global__ void k_hist_reduce2(const int* __restrict__ chunk_ptr, const double* __restrict__ partial, int C2,
+                               double* __restrict__ s1, double* __restrict__ s2) {
+    const int rb = blockIdx.x;
+    const int nout = T * C2;
+    const int c0 = chunk_ptr[rb], c1 = chunk_ptr[rb + 1];
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int c = c0; c < c1; c++) {
+            a += partial[(size_t)c * 2 * nout + o];
+            b += partial[(size_t)c * 2 * nout + nout + o];
+        }
+        s1[(size_t)rb * nout + o] = a;
+        s2[(size_t)rb * nout + o] = b;
+    }
+}
+
+// Y[M][N] (double) = A[M][K] (float, row-major, lda = K) * X[K][N] (float).
+// 128 x 64 output tile per CTA, 8 x 4 outputs per thread; FP32 products summed
+// in FP32 over 128 consecutive k, then added into FP64 accumulators.
+constexpr int SG_M = 128, SG_N = 64, SG_K = 16;
+__global__ void __launch_bounds__(256) k_sgemm_d(int M, int N, int K, const float* __restrict__ A,
+                                                 const float* __restrict__ X, double* __restrict__ Y) {
+    __shared__ float sa[SG_K][SG_M + 4];
+    __shared__ float sx[SG_K][SG_N];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads: 4 cols x 8 rows each
+    const int row0 = blockIdx.x * SG_M, col0 = blockIdx.y * SG_N;
+    float acc[8][4];
+    double dacc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            acc[i][j] = 0.f;
+            dacc[i][j] = 0.0;
+        }
+    int since = 0;
+    for (int k0 = 0; k0 < K; k0 += SG_K) {
+        for (int e = tid; e < SG_M * SG_K; e += 256) {
+            const int r = e / SG_K, k = e - r * SG_K;
+            const int gr = row0 + r, gk = k0 + k;
+            sa[k][r] = (gr < M && gk < K) ? A[(size_t)gr * K + gk] : 0.f;
+        }
+        for (int e = tid; e < SG_K * SG_N; e += 256) {
+            const int k = e / SG_N, c = e - k * SG_N;
+            const int gk = k0 + k, gc = col0 + c;
+            sx[k][c] = (gk < K && gc < N) ? X[(size_t)gk * N + gc] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SG_K; k++) {
+            float av[8], xv[4];
+#pragma unroll
+            for (int i = 0; i < 8; i++) av[i] = sa[k][ty * 8 + i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) xv[j] = sx[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+        }
+        __syncthreads();
+        since += SG_K;
+        if (since >= 128) {
+            since = 0;
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    dacc[i][j] += (double)acc[i][j];
+                    acc[i][j] = 0.f;
+                }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int r = row0 + ty * 8 + i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int c = col0 + tx * 4 + j;
+            if (c < N) Y[(size_t)r * N + c] = dacc[i][j] + (double)acc[i][j];
+        }
+    }
+}
+
+__global__ void k_d2f(size_t n, const double* __restrict__ x, float* __restrict__ y) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
+// Unit right-hand sides for the column-by-column assembly of a dense operator:
+// batch entry b selects column J = J0 + b of the (2 npad)-dimensional space
+// (interleaved index 2 q + c: edge q, component c). X is a block vector [npad][2B].
+__global__ void k_unit_cols(int npad, int B, long long J0, long long Jend, double* __restrict__ X) {
+    const int C2 = 2 * B;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)npad * C2;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(i / C2), cc = (int)(i % C2), c = cc / B, b = cc % B;
+        const long long J = J0 + b;
+        X[i] = (J < Jend && J == 2LL * q + c) ? 1.0 : 0.0;
+    }
+}
+
+// Dense[(2p+a) * ldd + J0 + b] = Y[p][a*B + b] for J0 + b < Jend (rows 2 npad)
+__global__ void k_scatter_cols(int npad, int B, long long J0, long long Jend, const double* __restrict__ Y,
+                               double* __restrict__ D, long long ldd) {
+    const int C2 = 2 * B;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)npad * C2;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(i / C2), cc = (int)(i % C2), a = cc / B, b = cc % B;
+        const long long J = J0 + b;
+        if (J < Jend) D[(size_t)(2LL * p + a) * ldd + J] = Y[i];
+    }
+}
+
+// Left-factor columns: batch entry b selects column q = Q0 + b of [M1 | M2]
+// (q < npad: unit u-part in y1; npad <= q < 2 npad: unit u-part in y2).
+__global__ void k_unit_lf(int npad, int B, long long Q0, long long Qend, double* __restrict__ y1,
+                          double* __restrict__ y2) {
+    const int C2 = 2 * B;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)npad * C2;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(i / C2), cc = (int)(i % C2);
+        const long long q = Q0 + (cc % B);
+        const bool upart = cc < B;
+        y1[i] = (upart && q < Qend && q < npad && q == p) ? 1.0 : 0.0;
+        y2[i] = (upart && q < Qend && q >= npad && q - npad == p) ? 1.0 : 0.0;
+    }
+}
+
+// LF[p * ldd + Q0 + b] = out[p][b] (u-part of the left factor applied to unit columns)
+__global__ void k_scatter_lf(int npad, int B, long long Q0, long long Qend, const double* __restrict__ out,
+                             double* __restrict__ D, long long ldd) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)npad * B;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(i / B), b = (int)(i % B);
+        if (Q0 + b < Qend) D[(size_t)p * ldd + Q0 + b] = out[(size_t)p * 2 * B + b];
+    }
+}
+
+inline int grid_for(size_t n, int bs = 256) {
+    size_t g = (n + bs - 1) / bs;
+    if (g > 65535ULL * 8) g = 65535ULL * 8;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+namespace mot {
+
+void launch_history32(mot_handle* h, const TaskList& tl, const float* tiles, const float* ring, const float* win,
+                      const float* kry, int mode, long long step_i, double* out_s1, double* out_s2,
+                      cudaStream_t s) {
+    const int C2 = 2 * h->B;
+    if (tl.nchunks > 0) {
+        const bool timed = h->opt.timing && mode == 0 && h->ev0 && step_i > h->K;
+        if (timed) cudaEventRecord(h->ev0, s);
+        k_hist_f32<<<tl.nchunks, NT, 0, s>>>(tl.tasks, tl.chunks, tiles, ring, win, kry, mode, step_i, h->R, h->npad,
+                                             C2, h->d_colidx, h->d_partial);
+        if (timed) {
+            cudaEventRecord(h->ev1, s);
+            h->ev_pending = true;
+        }
+        h->launches++;
+    }
+    k_hist_reduce2<<<h->nrb, 256, 0, s>>>(tl.chunk_ptr, h->d_partial, C2, out_s1, out_s2);
+    h->launches++;
+}
+
+void launch_sgemm_d(mot_handle* h, int M, int N, int K, const float* A, const float* X, double* Y, cudaStream_t s) {
+    dim3 grid((M + SG_M - 1) / SG_M, (N + SG_N - 1) / SG_N);
+    k_sgemm_d<<<grid, 256, 0, s>>>(M, N, K, A, X, Y);
+    h->launches++;
+}
+
+void launch_d2f(mot_handle* h, size_t n, const double* x, float* y, cudaStream_t s) {
+    k_d2f<<<grid_for(n), 256, 0, s>>>(n, x, y);
+    h->launches++;
+}
+
+void launch_unit_cols(mot_handle* h, long long J0, long long Jend, double* X, cudaStream_t s) {
+    k_unit_cols<<<grid_for((size_t)h->npad * 2 * h->B), 256, 0, s>>>(h->npad, h->B, J0, Jend, X);
+    h->launches++;
+}
+
+void launch_scatter_cols(mot_handle* h, long long J0, long long Jend, const double* Y, double* D, long long ldd,
+                         cudaStream_t s) {
+    k_scatter_cols<<<grid_for((size_t)h->npad * 2 * h->B), 256, 0, s>>>(h->npad, h->B, J0, Jend, Y, D, ldd);
+    h->launches++;
+}
+
+void launch_unit_lf(mot_handle* h, long long Q0, long long Qend, double* y1, double* y2, cudaStream_t s) {
+    k_unit_lf<<<grid_for((size_t)h->npad * 2 * h->B), 256, 0, s>>>(h->npad, h->B, Q0, Qend, y1, y2);
+    h->launches++;
+}
+
+void launch_scatter_lf(mot_handle* h, long long Q0, long long Qend, const double* out, double* D, long long ldd,
+                       cudaStream_t s) {
+    k_scatter_lf<<<grid_for((size_t)h->npad * h->B), 256, 0, s>>>(h->npad, h->B, Q0, Qend, out, D, ldd);
+    h->launches++;
+}
+
+}  // namespace mot

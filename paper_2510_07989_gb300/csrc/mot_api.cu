@@ -49,6 +49,18 @@ void* dalloc(mot_handle* h, size_t bytes) {
     return p;
 }
 
+// mixed-precision kernels (k_mixed.cu)
+void launch_history32(mot_handle* h, const TaskList& tl, const float* tiles, const float* ring, const float* win,
+                      const float* kry, int mode, long long step_i, double* out_s1, double* out_s2, cudaStream_t s);
+void launch_sgemm_d(mot_handle* h, int M, int N, int K, const float* A, const float* X, double* Y, cudaStream_t s);
+void launch_d2f(mot_handle* h, size_t n, const double* x, float* y, cudaStream_t s);
+void launch_unit_cols(mot_handle* h, long long J0, long long Jend, double* X, cudaStream_t s);
+void launch_scatter_cols(mot_handle* h, long long J0, long long Jend, const double* Y, double* D, long long ldd,
+                         cudaStream_t s);
+void launch_unit_lf(mot_handle* h, long long Q0, long long Qend, double* y1, double* y2, cudaStream_t s);
+void launch_scatter_lf(mot_handle* h, long long Q0, long long Qend, const double* out, double* D, long long ldd,
+                       cudaStream_t s);
+
 // extra launch wrappers (k_linalg.cu)
 void launch_pack2(mot_handle* h, const double* a, const double* b, int C, double* out, cudaStream_t s);
 void launch_unpack_q(mot_handle* h, const double* X, const double* P, int C, double* q1, double* q2, cudaStream_t s);
@@ -238,10 +250,27 @@ void left_factor(mot_handle* h, const Work& W, const double* y1, const double* y
     launch_axpby(h, n, 1.0, W.t1, 1.0, W.pd, out, s);   // P^{SH} t1 + P^L t2
 }
 
-// out = Q_0 v in product form
+bool mixed(const mot_handle* h) { return h->opt.precision == MOT_PREC_MIXED && h->d_Q0 && !h->precomputing; }
+bool mflag(const mot_handle* h, int bit) { return (h->opt.mixed_flags & bit) != 0; }
+
+// out = Q_0 v with the dense FP64 Q_0 (the refinement residual of the mixed path)
+void apply_q0_dense64(mot_handle* h, const double* v, double* out, cudaStream_t s) {
+    launch_gemm_rect(h, 2 * h->npad, 2 * h->npad, h->d_Q0, v, h->B, out, s);
+}
+
+// out = Q_0 v: dense Q_0 (mixed path, FP32 or FP64 copy) or the FP64 product form
 void apply_q0(mot_handle* h, const Work& W, const double* v, double* out, cudaStream_t s) {
     const int n = h->npad * 2 * h->B;
     const size_t bv = (size_t)n;
+    if (mixed(h)) {
+        if (mflag(h, MOT_MIX_Q032)) {
+            launch_d2f(h, bv, v, h->d_xf, s);
+            launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Q0f, h->d_xf, out, s);
+        } else {
+            apply_q0_dense64(h, v, out, s);
+        }
+        return;
+    }
     project_sigma(h, W, v, W.sig, s);
     launch_axpby(h, n, 1.0, v, -1.0, W.sig, W.ell, s);
     launch_variants(h, W.ell, W.kry, h->eta, h->etap, s);
@@ -250,14 +279,25 @@ void apply_q0(mot_handle* h, const Work& W, const double* v, double* out, cudaSt
     left_factor(h, W, W.y1, W.y2, out, s);
 }
 
-int gmres(mot_handle* h, const Work& W, const double* b, double* x, cudaStream_t s) {
+// GMRES on Q_0 x = b, started from the x passed in (x0 = 0 when have_x0 is
+// false); the relative tolerance always refers to |b|.
+int gmres(mot_handle* h, const Work& W, const double* b, double* x, bool have_x0, double tol, cudaStream_t s) {
     const int B = h->B;
     const size_t bv = (size_t)h->npad * 2 * B;
     const int m = h->gm_m;
-    CK(cudaMemsetAsync(x, 0, sizeof(double) * bv, s));
+    h->gm_tol = tol;
     launch_gm_norm(h, b, W.beta, s);
-    launch_gm_init(h, W.beta, 1, s);
-    launch_gm_scale(h, b, W.beta, h->d_V, s);
+    launch_gm_init(h, W.beta, 1, s);  // records |b| as the reference norm
+    if (have_x0) {
+        apply_q0(h, W, x, W.r, s);
+        launch_axpby(h, (int)bv, 1.0, b, -1.0, W.r, W.r, s);
+        launch_gm_norm(h, W.r, W.beta, s);
+        launch_gm_init(h, W.beta, 0, s);
+        launch_gm_scale(h, W.r, W.beta, h->d_V, s);
+    } else {
+        CK(cudaMemsetAsync(x, 0, sizeof(double) * bv, s));
+        launch_gm_scale(h, b, W.beta, h->d_V, s);
+    }
     int total = 0;
     bool converged = false;
     std::vector<int> act(B);
@@ -313,6 +353,15 @@ int ensure_state(mot_handle* h, int B) {
     h->d_ring = (double*)dalloc(h, sizeof(double) * (size_t)h->R * 6 * bv);
     h->d_win = (double*)dalloc(h, sizeof(double) * (size_t)(h->max_tail_lag + 1) * bv);
     h->d_cur = (double*)dalloc(h, sizeof(double) * 4 * (size_t)h->npad * B);
+    if (h->opt.precision == MOT_PREC_MIXED && !h->precomputing) {
+        h->d_ring32 = (float*)dalloc(h, sizeof(float) * (size_t)h->R * 6 * bv);
+        h->d_win32 = (float*)dalloc(h, sizeof(float) * (size_t)(h->max_tail_lag + 1) * bv);
+        h->d_xf = (float*)dalloc(h, sizeof(float) * 2 * bv);
+        if (!h->d_ring32 || !h->d_win32 || !h->d_xf) return fail(h, MOT_EOOM, "device allocation of the march state");
+    }
+    h->d_wprev1 = (double*)dalloc(h, sizeof(double) * bv);
+    h->d_wprev2 = (double*)dalloc(h, sizeof(double) * bv);
+    if (!h->d_wprev1 || !h->d_wprev2) return fail(h, MOT_EOOM, "device allocation of the march state");
     h->d_dft = (double*)dalloc(h, sizeof(double) * std::max(1, h->nfreq) * 4 * (size_t)h->npad * B * 2);
     h->work_bytes = sizeof(double) * work_doubles(h);
     h->d_work = (double*)dalloc(h, h->work_bytes);
@@ -340,9 +389,15 @@ int ensure_state(mot_handle* h, int B) {
 
 void free_state(mot_handle* h) {
     void* ptrs[] = {h->d_waves, h->d_ring, h->d_win, h->d_cur, h->d_dft, h->d_work, h->d_partial, h->d_V, h->d_H,
-                    h->d_g, h->d_cs, h->d_sn, h->d_red, h->d_resid, h->d_gm_active, h->d_gm_jend, h->d_gm_bnorm};
+                    h->d_g, h->d_cs, h->d_sn, h->d_red, h->d_resid, h->d_gm_active, h->d_gm_jend, h->d_gm_bnorm,
+                    h->d_wprev1, h->d_wprev2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    h->d_wprev1 = h->d_wprev2 = nullptr;
+    void* fptrs[] = {h->d_ring32, h->d_win32, h->d_xf};
+    for (void* p : fptrs)
+        if (p) cudaFree(p);
+    h->d_ring32 = h->d_win32 = h->d_xf = nullptr;
     h->d_waves = h->d_ring = h->d_win = h->d_cur = h->d_dft = h->d_work = h->d_partial = nullptr;
     h->d_V = h->d_H = h->d_g = h->d_cs = h->d_sn = h->d_red = h->d_resid = nullptr;
     h->d_gm_active = h->d_gm_jend = nullptr;
@@ -392,24 +447,79 @@ int do_step(mot_handle* h, cudaStream_t s) {
     const size_t bv = (size_t)n;
     CK(cudaMemsetAsync(h->d_cg_iters, 0, 2 * sizeof(int), s));
     launch_rhs(h, i, W.rho1, W.rho2, s);
+    const bool mx = mixed(h);
+    const bool h32 = mx && mflag(h, MOT_MIX_HIST32);
     if (i >= 2) {
         launch_window_sums(h, i, s);
-        launch_history(h, h->hist, h->d_tiles, h->d_ring, h->d_win, nullptr, 0, i, W.s1, W.s2, s);
+        if (h32) {
+            if (h->max_tail_lag >= 1) launch_d2f(h, (size_t)(h->max_tail_lag + 1) * bv, h->d_win, h->d_win32, s);
+            launch_history32(h, h->hist, h->d_tiles32, h->d_ring32, h->d_win32, nullptr, 0, i, W.s1, W.s2, s);
+        } else {
+            launch_history(h, h->hist, h->d_tiles, h->d_ring, h->d_win, nullptr, 0, i, W.s1, W.s2, s);
+        }
         launch_axpby(h, n, 1.0, W.rho1, -1.0, W.s1, W.y1, s);
         launch_axpby(h, n, 1.0, W.rho2, -1.0, W.s2, W.y2, s);
     } else {
         launch_axpby(h, n, 1.0, W.rho1, 0.0, nullptr, W.y1, s);
         launch_axpby(h, n, 1.0, W.rho2, 0.0, nullptr, W.y2, s);
     }
-    left_factor(h, W, W.y1, W.y2, W.b, s);
-    int st = gmres(h, W, W.b, W.x, s);
+    if (mx) {
+        // b = [M1 | M2] [y1; y2] (y1, y2 are adjacent block vectors)
+        if (mflag(h, MOT_MIX_LF32)) {
+            launch_d2f(h, 2 * bv, W.y1, h->d_xf, s);
+            launch_sgemm_d(h, h->npad, 2 * h->B, 2 * h->npad, h->d_LFf, h->d_xf, W.b, s);
+        } else {
+            launch_gemm_rect(h, h->npad, 2 * h->npad, h->d_LF, W.y1, 2 * h->B, W.b, s);
+        }
+    } else {
+        left_factor(h, W, W.y1, W.y2, W.b, s);
+    }
+    // initial guess: linear extrapolation of the last two solutions
+    bool have_x0 = i >= 2;
+    if (i >= 3)
+        launch_axpby(h, n, 2.0, h->d_wprev1, -1.0, h->d_wprev2, W.x, s);
+    else if (i == 2)
+        launch_axpby(h, n, 1.0, h->d_wprev1, 0.0, nullptr, W.x, s);
+    const bool refine = mx && mflag(h, MOT_MIX_REFINE);
+    // with refinement the reduced-precision solves only need 1e-6: each sweep gains ~6 digits
+    int st = gmres(h, W, W.b, W.x, have_x0, refine ? std::max(h->opt.gmres_tol, 1e-6) : h->opt.gmres_tol, s);
     if (st != MOT_OK && st != MOT_ENOCONV) return st;
+    h->refine_sweeps = 0;
+    if (refine) {
+        // FP64 iterative refinement: r = b - Q_0 x with the FP64 dense Q_0,
+        // correction from the reduced-precision GMRES, until |r| <= gmres_tol |b|
+        const int gm_iters = h->last_gmres_iters;
+        for (int sweep = 0; sweep < 3; sweep++) {
+            apply_q0_dense64(h, W.x, W.r, s);
+            launch_axpby(h, n, 1.0, W.b, -1.0, W.r, W.r, s);
+            launch_gm_norm(h, W.r, W.nrm, s);
+            launch_gm_norm(h, W.b, W.beta, s);
+            std::vector<double> rn(h->B), bn(h->B);
+            CK(cudaMemcpyAsync(rn.data(), W.nrm, sizeof(double) * h->B, cudaMemcpyDeviceToHost, s));
+            CK(cudaMemcpyAsync(bn.data(), W.beta, sizeof(double) * h->B, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            double worst = 0;
+            for (int b = 0; b < h->B; b++) worst = std::max(worst, bn[b] > 0 ? rn[b] / bn[b] : 0.0);
+            h->last_gmres_resid = worst;
+            if (worst <= h->opt.gmres_tol) break;
+            h->refine_sweeps++;
+            // W.tmp receives the correction d of Q_0 d = r (r copied to W.dd: gmres uses W.r)
+            launch_axpby(h, n, 1.0, W.r, 0.0, nullptr, W.dd, s);
+            int st2 = gmres(h, W, W.dd, W.tmp, false, 1e-6, s);
+            if (st2 != MOT_OK && st2 != MOT_ENOCONV) return st2;
+            launch_axpby(h, n, 1.0, W.x, 1.0, W.tmp, W.x, s);
+        }
+        h->last_gmres_iters = gm_iters;
+    }
+    std::swap(h->d_wprev1, h->d_wprev2);
+    CK(cudaMemcpyAsync(h->d_wprev1, W.x, sizeof(double) * bv, cudaMemcpyDeviceToDevice, s));
     // ring slot i: variants of l_i and s_i
     project_sigma(h, W, W.x, W.sig, s);
     launch_axpby(h, n, 1.0, W.x, -1.0, W.sig, W.ell, s);
     const int slot = (int)(i % h->R);
     launch_variants(h, W.ell, h->d_ring + ((size_t)slot * 2 + 0) * 3 * bv, h->eta, h->etap, s);
     launch_variants(h, W.sig, h->d_ring + ((size_t)slot * 2 + 1) * 3 * bv, h->eta, h->etap, s);
+    if (mx) launch_d2f(h, 6 * bv, h->d_ring + (size_t)slot * 6 * bv, h->d_ring32 + (size_t)slot * 6 * bv, s);
     h->step = i;
     launch_recover(h, i, s);
     CK(cudaGetLastError());
@@ -450,6 +560,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
         if (opt->cg_tol > 0) h->opt.cg_tol = opt->cg_tol;
         if (opt->cg_maxit > 0) h->opt.cg_maxit = opt->cg_maxit;
         h->opt.timing = opt->timing;
+        h->opt.mixed_flags = opt->mixed_flags;
     }
     auto bad = [&](const char* m) {
         h->err = m;
@@ -459,7 +570,9 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
     if (!mesh || !mesh->verts || !mesh->tris || mesh->nv < 4 || mesh->nf < 4) return bad("mesh missing or too small");
     if (!(eps_r > 0) || !(mu_r > 0) || !(dt > 0) || !std::isfinite(eps_r) || !std::isfinite(mu_r) || !std::isfinite(dt))
         return bad("eps_r, mu_r and dt must be finite and > 0");
-    if (h->opt.precision != MOT_PREC_FP64) return bad("only MOT_PREC_FP64 is available in this build");
+    if (h->opt.precision != MOT_PREC_FP64 && h->opt.precision != MOT_PREC_MIXED) return bad("unknown precision");
+    if (h->opt.precision == MOT_PREC_MIXED && !(opt && opt->gmres_tol > 0)) h->opt.gmres_tol = 1e-11;
+    if (h->opt.mixed_flags == 0) h->opt.mixed_flags = MOT_MIX_DEFAULT;
     h->nv = mesh->nv;
     h->nf = mesh->nf;
     h->verts.assign(mesh->verts, mesh->verts + 3 * (size_t)h->nv);
@@ -633,6 +746,46 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
     const int L = h->kmax + 2;  // lags 0 .. kmax+1
     std::vector<int> id((size_t)NTK * L * nrb * nrb, -1);
     auto key = [&](int kind, int k, int rb, int cb) { return (((size_t)kind * L + k) * nrb + rb) * nrb + cb; };
+    // Column order of every row block: all edges sorted by the distance of their
+    // midpoint from the block's centroid. Interactions are shell shaped (lag k
+    // couples edges about k c dt apart), so columns at similar distance share
+    // their nonzero lags and the (row block x 32 sorted columns) tiles are dense.
+    const int np = h->npad;
+    std::vector<double> mid(3 * (size_t)h->ne);
+    for (int p = 0; p < h->ne; p++) {
+        const int e = h->perm[p];
+        for (int d = 0; d < 3; d++)
+            mid[3 * p + d] = 0.5 * (h->verts[3 * h->ev[2 * e] + d] + h->verts[3 * h->ev[2 * e + 1] + d]);
+    }
+    std::vector<int> colidx((size_t)nrb * np, h->ne < np ? h->ne : 0), colpos((size_t)nrb * np, 0);
+    {
+        auto sort_rb = [&](int t0, int nth) {
+            std::vector<std::pair<double, int>> dist(h->ne);
+            for (int rb = t0; rb < nrb; rb += nth) {
+                double c[3] = {0, 0, 0};
+                int cnt = 0;
+                for (int p = rb * T; p < std::min(h->ne, rb * T + T); p++, cnt++)
+                    for (int d = 0; d < 3; d++) c[d] += mid[3 * p + d];
+                for (int d = 0; d < 3; d++) c[d] /= std::max(1, cnt);
+                for (int p = 0; p < h->ne; p++) {
+                    double dx = mid[3 * p] - c[0], dy = mid[3 * p + 1] - c[1], dz = mid[3 * p + 2] - c[2];
+                    dist[p] = {dx * dx + dy * dy + dz * dz, p};
+                }
+                std::sort(dist.begin(), dist.end());
+                for (int j = 0; j < h->ne; j++) {
+                    colidx[(size_t)rb * np + j] = dist[j].second;
+                    colpos[(size_t)rb * np + dist[j].second] = j;
+                }
+            }
+        };
+        int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> ths;
+        for (int t = 0; t < nth; t++) ths.emplace_back(sort_rb, t, nth);
+        for (auto& t : ths) t.join();
+    }
+    h->d_colidx = (int*)dalloc(h, sizeof(int) * colidx.size());
+    if (!h->d_colidx) return fail(h, MOT_EOOM, "device allocation (column order)");
+    CK(cudaMemcpy(h->d_colidx, colidx.data(), sizeof(int) * colidx.size(), cudaMemcpyHostToDevice));
     int max_tail = 0;
     // pass 1: validate and mark occupied tiles
     for (int mi = 0; mi < 12; mi++) {
@@ -649,7 +802,7 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
             for (int64_t e = M.rowptr[m]; e < M.rowptr[m + 1]; e++) {
                 const int n = M.col[e];
                 if (n < 0 || n >= h->ne) return fail(h, MOT_EINVAL, "lag matrix column out of range");
-                const int cb = h->iperm[n] / T;
+                const int cb = colpos[(size_t)rb * np + h->iperm[n]] / T;
                 const int k0 = M.k0[e], c = M.cnt[e];
                 if (k0 < 0 || c < 0) return fail(h, MOT_EINVAL, "negative lag window");
                 for (int k = k0; k < k0 + c; k++) {
@@ -698,7 +851,8 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
                 const int r = p - rb * T;
                 for (int64_t e = M.rowptr[m]; e < M.rowptr[m + 1]; e++) {
                     const int q = h->iperm[M.col[e]];
-                    const int cb = q / T, cc = q - cb * T;
+                    const int qs = colpos[(size_t)rb * np + q];
+                    const int cb = qs / T, cc = qs - cb * T;
                     for (int k = M.k0[e]; k < M.k0[e] + M.cnt[e] && k <= lagmax; k++) {
                         const double v = M.val[M.voff[e] + (k - M.k0[e])];
                         if (v == 0.0) continue;
@@ -814,6 +968,60 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
 
 }  // namespace
 
+namespace {
+
+// Mixed path set-up: dense Q_0 and [M1 | M2] assembled column by column from the
+// FP64 product form (64 unit columns per batch), then FP32 copies of them and of
+// the history tiles. The FP64 history tiles are released afterwards.
+int precompute_mixed(mot_handle* h) {
+    const int Bp = 64;
+    h->precomputing = true;
+    int st = ensure_state(h, Bp);
+    if (st != MOT_OK) return st;
+    Work W = work_of(h);
+    cudaStream_t s = 0;
+    const long long n2 = 2LL * h->npad;
+    h->d_Q0 = (double*)dalloc(h, sizeof(double) * (size_t)n2 * n2);
+    h->d_LF = (double*)dalloc(h, sizeof(double) * (size_t)h->npad * n2);
+    h->d_Q0f = (float*)dalloc(h, sizeof(float) * (size_t)n2 * n2);
+    h->d_LFf = (float*)dalloc(h, sizeof(float) * (size_t)h->npad * n2);
+    const bool h32 = (h->opt.mixed_flags & MOT_MIX_HIST32) != 0;
+    if (h32)
+        h->d_tiles32 =
+            (float*)dalloc(h, sizeof(float) * (size_t)std::max<int64_t>(1, h->ntiles) * MOT_TILE * MOT_TILE);
+    if (!h->d_Q0 || !h->d_LF || !h->d_Q0f || !h->d_LFf || (h32 && !h->d_tiles32))
+        return fail(h, MOT_EOOM, "device allocation (mixed-precision operators)");
+    CK(cudaMemsetAsync(h->d_cg_iters, 0, 2 * sizeof(int), s));
+    for (long long J0 = 0; J0 < n2; J0 += Bp) {
+        launch_unit_cols(h, J0, n2, W.x, s);
+        apply_q0(h, W, W.x, W.w, s);
+        launch_scatter_cols(h, J0, n2, W.w, h->d_Q0, n2, s);
+    }
+    for (long long Q0 = 0; Q0 < n2; Q0 += Bp) {
+        launch_unit_lf(h, Q0, n2, W.rho1, W.rho2, s);
+        left_factor(h, W, W.rho1, W.rho2, W.b, s);
+        launch_scatter_lf(h, Q0, n2, W.b, h->d_LF, n2, s);
+    }
+    launch_d2f(h, (size_t)n2 * n2, h->d_Q0, h->d_Q0f, s);
+    launch_d2f(h, (size_t)h->npad * n2, h->d_LF, h->d_LFf, s);
+    if (h32) launch_d2f(h, (size_t)h->ntiles * MOT_TILE * MOT_TILE, h->d_tiles, h->d_tiles32, s);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    int it[2];
+    CK(cudaMemcpy(it, h->d_cg_iters, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    free_state(h);
+    h->precomputing = false;
+    if (it[1] > 0) return fail(h, MOT_ENOCONV, "a CG solve did not converge while assembling the dense operators");
+    if (h32) {  // the FP64 history tiles are no longer read
+        cudaFree(h->d_tiles);
+        h->device_bytes -= (int64_t)(sizeof(double) * (size_t)std::max<int64_t>(1, h->ntiles) * MOT_TILE * MOT_TILE);
+        h->d_tiles = nullptr;
+    }
+    return MOT_OK;
+}
+
+}  // namespace
+
 MOT_API int mot_load_operators(mot_handle* h, const mot_operators* ops) {
     if (!h) return MOT_EINVAL;
     if (h->loaded) return fail(h, MOT_ESTATE, "operators already loaded");
@@ -870,6 +1078,7 @@ MOT_API int mot_load_operators(mot_handle* h, const mot_operators* ops) {
     CK(cudaMemcpy(h->d_rhs_x, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_rhs_wf, wf.data(), sizeof(double) * wf.size(), cudaMemcpyHostToDevice));
     if ((st = build_tiles(h, ops)) != MOT_OK) return st;
+    if (h->opt.precision == MOT_PREC_MIXED && (st = precompute_mixed(h)) != MOT_OK) return st;
     h->loaded = true;
     return MOT_OK;
 }
@@ -993,7 +1202,8 @@ MOT_API int mot_save_state(mot_handle* h, void* buf, size_t* size) {
     const size_t ring = sizeof(double) * (size_t)h->R * 6 * bv;
     const size_t cur = sizeof(double) * 4 * (size_t)h->npad * h->B;
     const size_t dft = sizeof(double) * std::max(1, h->nfreq) * 4 * (size_t)h->npad * h->B * 2;
-    const size_t need = sizeof(StateHeader) + sizeof(double) * 10 * h->B + ring + cur + dft;
+    const size_t wp = sizeof(double) * bv;
+    const size_t need = sizeof(StateHeader) + sizeof(double) * 10 * h->B + ring + cur + dft + 2 * wp;
     if (!buf) {
         *size = need;
         return MOT_OK;
@@ -1012,6 +1222,10 @@ MOT_API int mot_save_state(mot_handle* h, void* buf, size_t* size) {
     CK(cudaMemcpy(p, h->d_cur, cur, cudaMemcpyDeviceToHost));
     p += cur;
     CK(cudaMemcpy(p, h->d_dft, dft, cudaMemcpyDeviceToHost));
+    p += dft;
+    CK(cudaMemcpy(p, h->d_wprev1, wp, cudaMemcpyDeviceToHost));
+    p += wp;
+    CK(cudaMemcpy(p, h->d_wprev2, wp, cudaMemcpyDeviceToHost));
     *size = need;
     return MOT_OK;
 }
@@ -1035,7 +1249,8 @@ MOT_API int mot_load_state(mot_handle* h, const void* buf, size_t size) {
     const size_t ring = sizeof(double) * (size_t)h->R * 6 * bv;
     const size_t cur = sizeof(double) * 4 * (size_t)h->npad * h->B;
     const size_t dft = sizeof(double) * std::max(1, h->nfreq) * 4 * (size_t)h->npad * h->B * 2;
-    if (size < sizeof hd + sizeof(double) * 10 * h->B + ring + cur + dft)
+    const size_t wp = sizeof(double) * bv;
+    if (size < sizeof hd + sizeof(double) * 10 * h->B + ring + cur + dft + 2 * wp)
         return fail(h, MOT_EINVAL, "state buffer too small");
     const char* p = (const char*)buf + sizeof hd;
     h->h_waves.assign((const double*)p, (const double*)p + 10 * h->B);
@@ -1046,6 +1261,10 @@ MOT_API int mot_load_state(mot_handle* h, const void* buf, size_t size) {
     CK(cudaMemcpy(h->d_cur, p, cur, cudaMemcpyHostToDevice));
     p += cur;
     CK(cudaMemcpy(h->d_dft, p, dft, cudaMemcpyHostToDevice));
+    p += dft;
+    CK(cudaMemcpy(h->d_wprev1, p, wp, cudaMemcpyHostToDevice));
+    p += wp;
+    CK(cudaMemcpy(h->d_wprev2, p, wp, cudaMemcpyHostToDevice));
     h->step = hd.step;
     return MOT_OK;
 }
@@ -1096,7 +1315,8 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->Lv.rowptr, h->Lv.col, h->Lv.val, h->G.rowptr, h->G.col, h->G.val, h->Gt.rowptr,
                     h->Gt.col, h->Gt.val, h->d_T0s, h->d_T0h, h->d_rhs_x, h->d_rhs_wf, h->d_tiles,
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
-                    h->lag0.chunk_ptr, h->d_omega};
+                    h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
+                    h->d_LFf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);

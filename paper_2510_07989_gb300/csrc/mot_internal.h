@@ -94,6 +94,9 @@ struct mot_handle {
     double* d_ring = nullptr;      // [R][2 parts][3 variants][npad][2B]
     double* d_win = nullptr;       // [max_tail_lag+1][npad][2B]
     double* d_cur = nullptr;       // [4][npad][B] recovered currents of the last step
+    double* d_wprev1 = nullptr;    // w_{i-1}, w_{i-2} (internal layout): GMRES initial guess
+    double* d_wprev2 = nullptr;
+    int* d_colidx = nullptr;       // [nrb][npad] column order of each row block (distance sorted)
     int nfreq = 0;
     std::vector<double> omega;
     double* d_omega = nullptr;
@@ -130,6 +133,18 @@ struct mot_handle {
     // algorithmic work of a full-depth history contraction
     double hist_nnz_tasks = 0;   // sum over history tasks of the tile's nonzeros
     double hist_nnz_unique = 0;  // nonzeros of the stored tiles used by the history list
+    // mixed-precision path (MOT_PREC_MIXED)
+    float* d_tiles32 = nullptr;    // FP32 copy of the history tiles
+    float* d_ring32 = nullptr;     // FP32 copy of the coefficient ring
+    float* d_win32 = nullptr;      // FP32 windowed sums
+    double* d_Q0 = nullptr;        // dense Q_0, (2 npad)^2, interleaved (edge, component) order, FP64
+    float* d_Q0f = nullptr;        // FP32 copy
+    double* d_LF = nullptr;        // dense [M1 | M2], npad x 2 npad, FP64
+    float* d_LFf = nullptr;        // FP32 copy
+    float* d_xf = nullptr;         // FP32 staging: [2 bv]
+    bool precomputing = false;     // dense operators being assembled (use the product form)
+    double gm_tol = 1e-12;         // relative tolerance of the GMRES solve in progress
+    int refine_sweeps = 0;         // FP64 refinement sweeps used by the last step
     // CUDA-event timing of the history launches (mot_options.timing)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ev_pending = false;
@@ -161,6 +176,9 @@ void launch_spmv(mot_handle* h, const DCsr& A, const double* x, int C, double* y
 int launch_cg(mot_handle* h, const DCsr& A, const DCsr* A2, const double* f, int C, double* z, double* work,
               cudaStream_t s);  // returns max iterations or -1 on no convergence
 void launch_gemm(mot_handle* h, const double* A, const double* X, int C, double* Y, cudaStream_t s);
+// Y[M][C] = A[M][K] X[K][C], FP64
+void launch_gemm_rect(mot_handle* h, int M, int K, const double* A, const double* X, int C, double* Y,
+                      cudaStream_t s);
 void launch_rhs(mot_handle* h, long long i, double* rho1, double* rho2, cudaStream_t s);
 void launch_window_sums(mot_handle* h, long long i, cudaStream_t s);
 void launch_recover(mot_handle* h, long long i, cudaStream_t s);
