@@ -303,6 +303,9 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "RHS·steps/s", "h2d_bytes_per_step": 80 * B,
                     "d2h_bytes_per_step": 8 * 2 * ops.ne * B},
             "gpu_launches": (info1["gpu_launches"] - info0["gpu_launches"]),
+            "phase_ms_per_step": {name: round((info1["phase_ms"][k] - info0["phase_ms"][k]) / args.steps, 3)
+                                  for k, name in enumerate(["rhs", "history", "left_factor", "gmres", "refine",
+                                                            "projector_ring", "recover"])},
             "roofline": roof,
             "peaks": {"source": how, "hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}}
     if world == 1 and not args.no_cpu_baseline:

@@ -67,11 +67,13 @@ typedef struct {
                               MOT_MIX_HIST32: FP32 history tiles and panels
                               MOT_MIX_LF32:   FP32 dense left factor [M1 | M2]
                               MOT_MIX_Q032:   FP32 dense Q_0 in the GMRES iterations
-                              MOT_MIX_REFINE: FP64 iterative refinement of the Q_0 solve */
+                              MOT_MIX_REFINE: FP64 iterative refinement of the Q_0 solve
+                              MOT_MIX_PRECOND: right-preconditioned GMRES with an FP32
+                                 copy of Q_0^{-1} (LU with partial pivoting at load) */
 } mot_options;
 
-enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8,
-       MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE };
+enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8, MOT_MIX_PRECOND = 16,
+       MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND };
 
 /*
  * Lag-window sparse matrix (one family / medium of Section V-B):
@@ -153,6 +155,11 @@ typedef struct {
        1..K) timed so far and their summed CUDA-event duration */
     int64_t hist_timed_launches;
     double hist_timed_ms;
+    /* with mot_options.timing: summed CUDA-event time (ms) of the step phases:
+       [0] right-hand side, [1] history contraction, [2] left factor,
+       [3] Q_0 GMRES solve, [4] FP64 refinement, [5] projector + ring update,
+       [6] current recovery and Fourier sums */
+    double phase_ms[8];
 } mot_info;
 
 /*

@@ -61,6 +61,11 @@ void launch_unit_lf(mot_handle* h, long long Q0, long long Qend, double* y1, dou
 void launch_scatter_lf(mot_handle* h, long long Q0, long long Qend, const double* out, double* D, long long ldd,
                        cudaStream_t s);
 
+// dense factorisation (k_dense.cu)
+int dense_lu(mot_handle* h, int n, double* A, int* piv, int* d_bad, cudaStream_t s);
+void dense_pad_identity(mot_handle* h, int n, int ne, double* A, cudaStream_t s);
+void dense_inverse_from_lu(mot_handle* h, int n, const double* LU, const int* piv, double* X, cudaStream_t s);
+
 // extra launch wrappers (k_linalg.cu)
 void launch_pack2(mot_handle* h, const double* a, const double* b, int C, double* out, cudaStream_t s);
 void launch_unpack_q(mot_handle* h, const double* X, const double* P, int C, double* q1, double* q2, cudaStream_t s);
@@ -263,11 +268,17 @@ void apply_q0(mot_handle* h, const Work& W, const double* v, double* out, cudaSt
     const int n = h->npad * 2 * h->B;
     const size_t bv = (size_t)n;
     if (mixed(h)) {
-        if (mflag(h, MOT_MIX_Q032)) {
+        const double* in = v;
+        if (h->prec_active) {  // right preconditioning: Q_0 (M v)
             launch_d2f(h, bv, v, h->d_xf, s);
+            launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Minvf, h->d_xf, W.q1, s);
+            in = W.q1;
+        }
+        if (mflag(h, MOT_MIX_Q032)) {
+            launch_d2f(h, bv, in, h->d_xf, s);
             launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Q0f, h->d_xf, out, s);
         } else {
-            apply_q0_dense64(h, v, out, s);
+            apply_q0_dense64(h, in, out, s);
         }
         return;
     }
@@ -341,6 +352,17 @@ int gmres(mot_handle* h, const Work& W, const double* b, double* x, bool have_x0
     h->last_gmres_resid = 0;
     for (double r : res) h->last_gmres_resid = std::max(h->last_gmres_resid, r);
     return converged ? MOT_OK : fail(h, MOT_ENOCONV, "GMRES reached its iteration limit");
+}
+
+// x solves Q_0 x = rhs by right-preconditioned GMRES: Q_0 M z = rhs, x = M z,
+// with M the FP32 copy of Q_0^{-1} (rhs must not be W.r, W.pd or W.q1)
+int prec_solve(mot_handle* h, const Work& W, const double* rhs, double* x, double tol, cudaStream_t s) {
+    h->prec_active = true;
+    int st = gmres(h, W, rhs, W.pd, false, tol, s);
+    h->prec_active = false;
+    launch_d2f(h, (size_t)h->npad * 2 * h->B, W.pd, h->d_xf, s);
+    launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Minvf, h->d_xf, x, s);
+    return st;
 }
 
 int ensure_state(mot_handle* h, int B) {
@@ -446,7 +468,11 @@ int do_step(mot_handle* h, cudaStream_t s) {
     const int n = h->npad * 2 * h->B;
     const size_t bv = (size_t)n;
     CK(cudaMemsetAsync(h->d_cg_iters, 0, 2 * sizeof(int), s));
+#define PEV(k) \
+    if (h->pev[0]) cudaEventRecord(h->pev[k], s)
+    PEV(0);
     launch_rhs(h, i, W.rho1, W.rho2, s);
+    PEV(1);
     const bool mx = mixed(h);
     const bool h32 = mx && mflag(h, MOT_MIX_HIST32);
     if (i >= 2) {
@@ -463,6 +489,7 @@ int do_step(mot_handle* h, cudaStream_t s) {
         launch_axpby(h, n, 1.0, W.rho1, 0.0, nullptr, W.y1, s);
         launch_axpby(h, n, 1.0, W.rho2, 0.0, nullptr, W.y2, s);
     }
+    PEV(2);
     if (mx) {
         // b = [M1 | M2] [y1; y2] (y1, y2 are adjacent block vectors)
         if (mflag(h, MOT_MIX_LF32)) {
@@ -474,6 +501,7 @@ int do_step(mot_handle* h, cudaStream_t s) {
     } else {
         left_factor(h, W, W.y1, W.y2, W.b, s);
     }
+    PEV(3);
     // initial guess: linear extrapolation of the last two solutions
     bool have_x0 = i >= 2;
     if (i >= 3)
@@ -481,9 +509,12 @@ int do_step(mot_handle* h, cudaStream_t s) {
     else if (i == 2)
         launch_axpby(h, n, 1.0, h->d_wprev1, 0.0, nullptr, W.x, s);
     const bool refine = mx && mflag(h, MOT_MIX_REFINE);
+    const bool prec = mx && h->d_Minvf;
     // with refinement the reduced-precision solves only need 1e-6: each sweep gains ~6 digits
-    int st = gmres(h, W, W.b, W.x, have_x0, refine ? std::max(h->opt.gmres_tol, 1e-6) : h->opt.gmres_tol, s);
+    const double tol_in = refine ? std::max(h->opt.gmres_tol, 1e-6) : h->opt.gmres_tol;
+    int st = prec ? prec_solve(h, W, W.b, W.x, tol_in, s) : gmres(h, W, W.b, W.x, have_x0, tol_in, s);
     if (st != MOT_OK && st != MOT_ENOCONV) return st;
+    PEV(4);
     h->refine_sweeps = 0;
     if (refine) {
         // FP64 iterative refinement: r = b - Q_0 x with the FP64 dense Q_0,
@@ -505,12 +536,13 @@ int do_step(mot_handle* h, cudaStream_t s) {
             h->refine_sweeps++;
             // W.tmp receives the correction d of Q_0 d = r (r copied to W.dd: gmres uses W.r)
             launch_axpby(h, n, 1.0, W.r, 0.0, nullptr, W.dd, s);
-            int st2 = gmres(h, W, W.dd, W.tmp, false, 1e-6, s);
+            int st2 = prec ? prec_solve(h, W, W.dd, W.tmp, 1e-6, s) : gmres(h, W, W.dd, W.tmp, false, 1e-6, s);
             if (st2 != MOT_OK && st2 != MOT_ENOCONV) return st2;
             launch_axpby(h, n, 1.0, W.x, 1.0, W.tmp, W.x, s);
         }
         h->last_gmres_iters = gm_iters;
     }
+    PEV(5);
     std::swap(h->d_wprev1, h->d_wprev2);
     CK(cudaMemcpyAsync(h->d_wprev1, W.x, sizeof(double) * bv, cudaMemcpyDeviceToDevice, s));
     // ring slot i: variants of l_i and s_i
@@ -520,11 +552,21 @@ int do_step(mot_handle* h, cudaStream_t s) {
     launch_variants(h, W.ell, h->d_ring + ((size_t)slot * 2 + 0) * 3 * bv, h->eta, h->etap, s);
     launch_variants(h, W.sig, h->d_ring + ((size_t)slot * 2 + 1) * 3 * bv, h->eta, h->etap, s);
     if (mx) launch_d2f(h, 6 * bv, h->d_ring + (size_t)slot * 6 * bv, h->d_ring32 + (size_t)slot * 6 * bv, s);
+    PEV(6);
     h->step = i;
     launch_recover(h, i, s);
+    PEV(7);
+#undef PEV
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_cg_iters, h->d_cg_iters, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (h->pev[0]) {
+        for (int k = 0; k < 7; k++) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, h->pev[k], h->pev[k + 1]));
+            h->phase_ms[k] += ms;
+        }
+    }
     if (h->ev_pending) {
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
@@ -723,6 +765,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
     if (h->opt.timing) {
         CK(cudaEventCreate(&h->ev0));
         CK(cudaEventCreate(&h->ev1));
+        for (int k = 0; k < 8; k++) CK(cudaEventCreate(&h->pev[k]));
     }
     int st;
     if ((st = upload_csr(h, VE, h->vtx_edges)) != MOT_OK) return st;
@@ -1005,6 +1048,30 @@ int precompute_mixed(mot_handle* h) {
     launch_d2f(h, (size_t)n2 * n2, h->d_Q0, h->d_Q0f, s);
     launch_d2f(h, (size_t)h->npad * n2, h->d_LF, h->d_LFf, s);
     if (h32) launch_d2f(h, (size_t)h->ntiles * MOT_TILE * MOT_TILE, h->d_tiles, h->d_tiles32, s);
+    if (h->opt.mixed_flags & MOT_MIX_PRECOND) {
+        // GMRES preconditioner: Q_0^{-1} by LU with partial pivoting (FP64), kept in FP32
+        double* lu = (double*)dalloc(h, sizeof(double) * (size_t)n2 * n2);
+        double* inv = (double*)dalloc(h, sizeof(double) * (size_t)n2 * n2);
+        int* piv = (int*)dalloc(h, sizeof(int) * (size_t)(n2 + 1));
+        h->d_Minvf = (float*)dalloc(h, sizeof(float) * (size_t)n2 * n2);
+        if (!lu || !inv || !piv || !h->d_Minvf) return fail(h, MOT_EOOM, "device allocation (Q_0 factorisation)");
+        CK(cudaMemcpyAsync(lu, h->d_Q0, sizeof(double) * (size_t)n2 * n2, cudaMemcpyDeviceToDevice, s));
+        dense_pad_identity(h, (int)n2, h->ne, lu, s);
+        const int bad = dense_lu(h, (int)n2, lu, piv, piv + n2, s);
+        if (bad > 0) {
+            cudaFree(lu);
+            cudaFree(inv);
+            cudaFree(piv);
+            return fail(h, MOT_EINVAL, "Q_0 is singular to working precision (LU pivot breakdown)");
+        }
+        dense_inverse_from_lu(h, (int)n2, lu, piv, inv, s);
+        launch_d2f(h, (size_t)n2 * n2, inv, h->d_Minvf, s);
+        CK(cudaDeviceSynchronize());
+        cudaFree(lu);
+        cudaFree(inv);
+        cudaFree(piv);
+        h->device_bytes -= (int64_t)(2 * sizeof(double) * (size_t)n2 * n2 + sizeof(int) * (size_t)(n2 + 1));
+    }
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     int it[2];
@@ -1293,6 +1360,7 @@ MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
     info->hist_bytes_per_step = 8.0 * h->hist_nnz_unique + 8.0 * (double)h->K * 2.0 * 2.0 * h->ne * Bc;
     info->hist_timed_launches = h->timed_launches;
     info->hist_timed_ms = h->timed_ms;
+    for (int k = 0; k < 8; k++) info->phase_ms[k] = h->phase_ms[k];
     return MOT_OK;
 }
 
@@ -1316,11 +1384,13 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->Gt.col, h->Gt.val, h->d_T0s, h->d_T0h, h->d_rhs_x, h->d_rhs_wf, h->d_tiles,
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
                     h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
-                    h->d_LFf};
+                    h->d_LFf, h->d_Minvf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    for (int k = 0; k < 8; k++)
+        if (h->pev[k]) cudaEventDestroy(h->pev[k]);
     delete h;
 }

@@ -142,11 +142,15 @@ struct mot_handle {
     double* d_LF = nullptr;        // dense [M1 | M2], npad x 2 npad, FP64
     float* d_LFf = nullptr;        // FP32 copy
     float* d_xf = nullptr;         // FP32 staging: [2 bv]
+    float* d_Minvf = nullptr;      // FP32 Q_0^{-1} (GMRES preconditioner), (2 npad)^2
+    bool prec_active = false;      // apply_q0 computes Q_0 M v
     bool precomputing = false;     // dense operators being assembled (use the product form)
     double gm_tol = 1e-12;         // relative tolerance of the GMRES solve in progress
     int refine_sweeps = 0;         // FP64 refinement sweeps used by the last step
     // CUDA-event timing of the history launches (mot_options.timing)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t pev[8] = {nullptr};  // step phase boundaries
+    double phase_ms[8] = {0};
     bool ev_pending = false;
     int64_t timed_launches = 0;
     double timed_ms = 0;
