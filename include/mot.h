@@ -57,7 +57,7 @@ typedef struct {
 typedef struct {
     int32_t precision;     /* MOT_PREC_FP64 (default) */
     int32_t device;        /* CUDA device ordinal, default 0 */
-    double gmres_tol;      /* relative residual of the Q_0 solve, default 1e-12 */
+    double gmres_tol;      /* relative residual of the Q_0 solve, default 1e-13 (FP64), 1e-11 (mixed) */
     int32_t gmres_maxit;   /* default 200 */
     double cg_tol;         /* relative residual of Laplacian / Gram solves, default 1e-14 */
     int32_t cg_maxit;      /* default 5000 */

@@ -90,6 +90,116 @@ __global__ void __launch_bounds__(NT) k_hist_f32(const HistTask* __restrict__ ta
     }
 }
 
+// Batched variant for 2B = 128 columns: 128 threads, each owning a 4 x 8 block
+// of the 32 x 128 output; tile and gathered panel rows double-buffered with
+// cp.async; FP32 register sums added into FP64 shared-memory accumulators when
+// the output target changes or every FLUSH tiles.
+constexpr int V2_C = 128, V2_AS = T + 4, V2_BS = V2_C + 4;
+
+__device__ __forceinline__ void cp16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__global__ void __launch_bounds__(128) k_hist_f32_b128(const HistTask* __restrict__ tasks,
+                                                      const HistChunk* __restrict__ chunks,
+                                                      const float* __restrict__ tiles, const float* __restrict__ ring,
+                                                      const float* __restrict__ win, long long step_i, int R,
+                                                      int npad, const int* __restrict__ colidx,
+                                                      double* __restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* acc64 = reinterpret_cast<double*>(smraw);                    // [2][T][V2_C]
+    float* sA = reinterpret_cast<float*>(smraw + sizeof(double) * 2 * T * V2_C);  // [2][T][V2_AS]
+    float* sB = sA + 2 * T * V2_AS;                                      // [2][T][V2_BS]
+    const HistChunk ch = chunks[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;  // columns tx*8..+7, rows ty*4..+3
+    for (int e = tid; e < 2 * T * V2_C; e += 128) acc64[e] = 0.0;
+    // compact the live tasks of this chunk: skip history before step 1
+    auto live = [&](int t) { return step_i - tasks[t].k >= 1; };
+    auto issue = [&](int t, int buf) {
+        const HistTask tk = tasks[t];
+        const int part = tk.code & 3, variant = (tk.code >> 2) & 3;
+        const float* pan = panel_ptr32(0, ring, win, nullptr, step_i, R, npad, V2_C, tk.k, part, variant);
+        const int* cols = colidx + (size_t)ch.rb * npad + (size_t)tk.cb * T;
+        const float* tl = tiles + (size_t)tk.tile * T * T;
+        float* a = sA + buf * T * V2_AS;
+        float* b = sB + buf * T * V2_BS;
+        for (int e = tid; e < T * (T / 4); e += 128) {  // 32 rows x 8 chunks of 16 B
+            const int r = e >> 3, c4 = (e & 7) * 4;
+            cp16(a + r * V2_AS + c4, tl + r * T + c4);
+        }
+        for (int e = tid; e < T * (V2_C / 4); e += 128) {  // 32 gathered rows x 32 chunks
+            const int r = e >> 5, c4 = (e & 31) * 4;
+            cp16(b + r * V2_BS + c4, pan + (size_t)cols[r] * V2_C + c4);
+        }
+    };
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 8; j++) acc[i][j] = 0.f;
+    int cur_out = -1, pending = 0;
+    auto flush = [&]() {
+        if (cur_out < 0) return;
+        double* d = acc64 + cur_out * T * V2_C;
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                d[(ty * 4 + i) * V2_C + tx * 8 + j] += (double)acc[i][j];
+                acc[i][j] = 0.f;
+            }
+        pending = 0;
+    };
+    const int t_end = ch.first + ch.count;
+    int t = ch.first;
+    while (t < t_end && !live(t)) t++;
+    int buf = 0;
+    if (t < t_end) issue(t, 0);
+    cp_commit();
+    while (t < t_end) {
+        int tn = t + 1;
+        while (tn < t_end && !live(tn)) tn++;
+        if (tn < t_end) issue(tn, buf ^ 1);
+        cp_commit();
+        cp_wait1();
+        __syncthreads();
+        const int out = (tasks[t].code >> 4) & 1;
+        if (out != cur_out || pending == FLUSH) {
+            flush();
+            cur_out = out;
+        }
+        const float* a = sA + buf * T * V2_AS;
+        const float* b = sB + buf * T * V2_BS;
+#pragma unroll 4
+        for (int k = 0; k < T; k++) {
+            float av[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) av[i] = a[(ty * 4 + i) * V2_AS + k];
+            const float4 b0 = *reinterpret_cast<const float4*>(b + k * V2_BS + tx * 8);
+            const float4 b1 = *reinterpret_cast<const float4*>(b + k * V2_BS + tx * 8 + 4);
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 8; j++) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        pending++;
+        __syncthreads();
+        buf ^= 1;
+        t = tn;
+    }
+    cp_wait0();
+    flush();
+    __syncthreads();
+    double* dst = partial + (size_t)blockIdx.x * 2 * T * V2_C;
+    for (int e = tid; e < 2 * T * V2_C; e += 128) dst[e] = acc64[e];
+}
+
 __global__ void k_hist_reduce2(const int* __restrict__ chunk_ptr, const double* __restrict__ partial, int C2,
                                double* __restrict__ s1, double* __restrict__ s2) {
     const int rb = blockIdx.x;
@@ -249,8 +359,19 @@ void launch_history32(mot_handle* h, const TaskList& tl, const float* tiles, con
     if (tl.nchunks > 0) {
         const bool timed = h->opt.timing && mode == 0 && h->ev0 && step_i > h->K;
         if (timed) cudaEventRecord(h->ev0, s);
-        k_hist_f32<<<tl.nchunks, NT, 0, s>>>(tl.tasks, tl.chunks, tiles, ring, win, kry, mode, step_i, h->R, h->npad,
-                                             C2, h->d_colidx, h->d_partial);
+        if (C2 == V2_C && mode == 0) {
+            const size_t smem = sizeof(double) * 2 * T * V2_C + sizeof(float) * 2 * T * (V2_AS + V2_BS);
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_hist_f32_b128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                attr = true;
+            }
+            k_hist_f32_b128<<<tl.nchunks, 128, smem, s>>>(tl.tasks, tl.chunks, tiles, ring, win, step_i, h->R,
+                                                          h->npad, h->d_colidx, h->d_partial);
+        } else {
+            k_hist_f32<<<tl.nchunks, NT, 0, s>>>(tl.tasks, tl.chunks, tiles, ring, win, kry, mode, step_i, h->R,
+                                                 h->npad, C2, h->d_colidx, h->d_partial);
+        }
         if (timed) {
             cudaEventRecord(h->ev1, s);
             h->ev_pending = true;

@@ -590,7 +590,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
     mot_handle* h = new mot_handle();
     h->opt.precision = MOT_PREC_FP64;
     h->opt.device = 0;
-    h->opt.gmres_tol = 1e-12;
+    h->opt.gmres_tol = 1e-13;
     h->opt.gmres_maxit = 200;
     h->opt.cg_tol = 1e-14;
     h->opt.cg_maxit = 5000;
@@ -965,6 +965,8 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
         std::iota(order.begin(), order.end(), 0);
         std::sort(order.begin(), order.end(), [&](int a, int b) {
             if (rbs[a] != rbs[b]) return rbs[a] < rbs[b];
+            const int oa = (tasks[a].code >> 4) & 1, ob = (tasks[b].code >> 4) & 1;
+            if (oa != ob) return oa < ob;  // contiguous runs per output target
             if (tasks[a].k != tasks[b].k) return tasks[a].k < tasks[b].k;
             return tasks[a].cb < tasks[b].cb;
         });

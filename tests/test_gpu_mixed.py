@@ -35,6 +35,19 @@ def test_mixed_pr1_matches_oracle(M, pr1_ops, pr1_system):
     assert err < TOL_MIXED
 
 
+def test_mixed_full_batch_pr1(M, pr1_ops, pr1_system):
+    """B = 64 (the batched-kernel width of the bench), PR1, sampled columns vs the oracle."""
+    exc = MS.fibonacci_batch(64, pr1_ops.dt, w_steps=30, t0_steps=60)
+    n = 150
+    W = M.Solver(pr1_ops, precision=M.MOT_PREC_MIXED).run(exc, n)
+    errs = []
+    for b in (0, 1, 17, 31, 32, 50, 63):
+        ref = O.march(pr1_system, exc, n, b=b)
+        errs.append(rel(W[:, b].reshape(n, -1), ref))
+    print("mixed PR1 B=64 max rel errs", ["%.3e" % e for e in errs])
+    assert max(errs) < TOL_MIXED
+
+
 def test_mixed_ragged_batch_l2(M):
     ops = assemble(MS.icosphere(2), 3.0, 1.0, 0.3)
     S = O.build_system(ops)
