@@ -70,6 +70,8 @@ typedef struct {
                               MOT_MIX_REFINE: FP64 iterative refinement of the Q_0 solve
                               MOT_MIX_PRECOND: right-preconditioned GMRES with an FP32
                                  copy of Q_0^{-1} (LU with partial pivoting at load) */
+    int32_t refine_sweeps; /* MOT_MIX_REFINE: FP64 residual + correction sweeps per step
+                              (stops early once |r| <= gmres_tol |b|); default 1 */
 } mot_options;
 
 enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8, MOT_MIX_PRECOND = 16,

@@ -161,6 +161,68 @@ __global__ void k_pad_identity(int n, int ne, double* __restrict__ A) {
         A[(size_t)J * n + J] = 1.0;
 }
 
+// A (npd x npd) = L + (1/n) 1 1^T on the leading n x n block (L in CSR), identity on the padding
+__global__ void k_lap_plus_j(int n, int npd, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const double* __restrict__ va, double* __restrict__ A) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)npd * npd;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / npd), j = (int)(e % npd);
+        A[e] = (i < n && j < n) ? 1.0 / n : (i == j ? 1.0 : 0.0);
+    }
+}
+__global__ void k_lap_add_csr(int n, int npd, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const double* __restrict__ va, double* __restrict__ A) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int j = rp[i]; j < rp[i + 1]; j++) A[(size_t)i * npd + ci[j]] += va[j];
+}
+
+// per-column dot products of two N x C row-major blocks: partial[chunk][c]
+__global__ void k_coldot(int N, int C, const double* __restrict__ X, const double* __restrict__ Y,
+                         double* __restrict__ partial) {
+    const int c = threadIdx.x % C, rs = threadIdx.x / C, RS = blockDim.x / C;
+    double s = 0.0;
+    if (threadIdx.x < RS * C)
+        for (int r = blockIdx.x * 64 + rs; r < min(N, blockIdx.x * 64 + 64); r += RS)
+            s = fma(X[(size_t)r * C + c], Y[(size_t)r * C + c], s);
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        double t = 0.0;
+        for (int k = 0; k < RS; k++) t += red[k * C + threadIdx.x];
+        partial[(size_t)blockIdx.x * C + threadIdx.x] = t;
+    }
+}
+__global__ void k_coldot_reduce(int nchunk, int C, const double* __restrict__ partial, double* __restrict__ out) {
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < nchunk; k++) s += partial[(size_t)k * C + c];
+        out[c] = s;
+    }
+}
+// x += a p ; r -= a q with a = num/den per column (0 if den <= 0 or the column is done)
+__global__ void k_pcg_xr(int N, int C, const double* __restrict__ num, const double* __restrict__ den,
+                         const int* __restrict__ done, const double* __restrict__ p, const double* __restrict__ q,
+                         double* __restrict__ x, double* __restrict__ r) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)N * C;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        const double a = (!done[c] && den[c] > 0.0) ? num[c] / den[c] : 0.0;
+        x[e] += a * p[e];
+        r[e] -= a * q[e];
+    }
+}
+// p = z + (num/den) p per column
+__global__ void k_pcg_p(int N, int C, const double* __restrict__ num, const double* __restrict__ den,
+                        const double* __restrict__ z, double* __restrict__ p) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)N * C;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e % C);
+        const double b = den[c] > 0.0 ? num[c] / den[c] : 0.0;
+        p[e] = z[e] + b * p[e];
+    }
+}
+
 inline void dgemm_sub(mot_handle* h, int M, int N, int K, const double* A, int lda, const double* B, int ldb,
                       double* C, int ldc, cudaStream_t s) {
     if (M <= 0 || N <= 0 || K <= 0) return;
@@ -172,6 +234,86 @@ inline void dgemm_sub(mot_handle* h, int M, int N, int K, const double* A, int l
 }  // namespace
 
 namespace mot {
+
+void launch_sgemm_d(mot_handle* h, int M, int N, int K, const float* A, const float* X, double* Y, cudaStream_t s);
+void launch_d2f(mot_handle* h, size_t n, const double* x, float* y, cudaStream_t s);
+
+void dense_lap_plus_j(mot_handle* h, const DCsr& L, int npd, double* A, cudaStream_t s) {
+    k_lap_plus_j<<<1024, 256, 0, s>>>(L.n, npd, L.rowptr, L.col, L.val, A);
+    k_lap_add_csr<<<(L.n + 255) / 256, 256, 0, s>>>(L.n, npd, L.rowptr, L.col, L.val, A);
+    h->launches += 2;
+}
+
+// Preconditioned FP64 CG on a graph Laplacian L (CSR, N rows) for C columns:
+// L z = f with f orthogonal to the constants, M an FP32 copy of (L + 11^T/N)^{-1}
+// (npd x npd, npd >= N, zero padded rows). work: 5 blocks of npd x C doubles,
+// d_scal: 6*C doubles + C ints, fstage: npd*C floats. Returns iterations (or -1).
+int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const double* f, int C, double* z,
+                   double* work, double* d_scal, float* fstage, double tol, int maxit, cudaStream_t s) {
+    const int N = L.n;
+    const size_t blk = (size_t)npd * C;
+    double* r = work;
+    double* p = r + blk;
+    double* q = p + blk;
+    double* zz = q + blk;
+    double* red = zz + blk;  // partials: ceil(npd/64) * C
+    double* rz = d_scal;
+    double* rzn = rz + C;
+    double* pq = rzn + C;
+    double* rr = pq + C;
+    double* ff = rr + C;
+    int* done = (int*)(ff + C);
+    const int nch = (N + 63) / 64;
+    auto coldot = [&](const double* X, const double* Y, double* out) {
+        k_coldot<<<nch, 256, 0, s>>>(N, C, X, Y, red);
+        k_coldot_reduce<<<1, 256, 0, s>>>(nch, C, red, out);
+        h->launches += 2;
+    };
+    auto precond = [&](const double* in, double* out) {  // out = M in (rows npd, FP32 products, FP64 sums)
+        launch_d2f(h, blk, in, fstage, s);
+        launch_sgemm_d(h, npd, C, npd, M, fstage, out, s);
+    };
+    const int g = (int)std::min<size_t>(4096, (blk + 255) / 256);
+    cudaMemsetAsync(z, 0, sizeof(double) * blk, s);
+    cudaMemsetAsync(done, 0, sizeof(int) * C, s);
+    cudaMemsetAsync(r, 0, sizeof(double) * blk, s);  // padded rows must be zero (finite) for M
+    cudaMemcpyAsync(r, f, sizeof(double) * (size_t)N * C, cudaMemcpyDeviceToDevice, s);
+    coldot(f, f, ff);
+    precond(r, zz);
+    cudaMemcpyAsync(p, zz, sizeof(double) * blk, cudaMemcpyDeviceToDevice, s);
+    coldot(r, zz, rz);
+    std::vector<double> hr(C), hf(C);
+    std::vector<int> hd(C, 0);
+    cudaMemcpyAsync(hf.data(), ff, sizeof(double) * C, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    int it = 0;
+    for (; it < maxit; it++) {
+        // q = L p
+        launch_spmv(h, L, p, C, q, s);
+        coldot(p, q, pq);
+        k_pcg_xr<<<g, 256, 0, s>>>(N, C, rz, pq, done, p, q, z, r);
+        coldot(r, r, rr);
+        cudaMemcpyAsync(hr.data(), rr, sizeof(double) * C, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        h->launches++;
+        bool all = true;
+        for (int c = 0; c < C; c++) {
+            if (!hd[c] && !(hr[c] > tol * tol * hf[c])) hd[c] = 1;
+            all &= hd[c] != 0;
+        }
+        if (all) {
+            it++;
+            break;
+        }
+        cudaMemcpyAsync(done, hd.data(), sizeof(int) * C, cudaMemcpyHostToDevice, s);
+        precond(r, zz);
+        coldot(r, zz, rzn);
+        k_pcg_p<<<g, 256, 0, s>>>(N, C, rzn, rz, zz, p);
+        cudaMemcpyAsync(rz, rzn, sizeof(double) * C, cudaMemcpyDeviceToDevice, s);
+        h->launches++;
+    }
+    return it;
+}
 
 void dense_pad_identity(mot_handle* h, int n, int ne, double* A, cudaStream_t s) {
     if (2 * ne >= n) return;

@@ -64,6 +64,9 @@ void launch_scatter_lf(mot_handle* h, long long Q0, long long Qend, const double
 // dense factorisation (k_dense.cu)
 int dense_lu(mot_handle* h, int n, double* A, int* piv, int* d_bad, cudaStream_t s);
 void dense_pad_identity(mot_handle* h, int n, int ne, double* A, cudaStream_t s);
+void dense_lap_plus_j(mot_handle* h, const DCsr& L, int npd, double* A, cudaStream_t s);
+int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const double* f, int C, double* z,
+                   double* work, double* d_scal, float* fstage, double tol, int maxit, cudaStream_t s);
 void dense_inverse_from_lu(mot_handle* h, int n, const double* LU, const int* piv, double* X, cudaStream_t s);
 
 // extra launch wrappers (k_linalg.cu)
@@ -222,11 +225,16 @@ size_t work_doubles(mot_handle* h) {
     return n;
 }
 
-// out = P^Sigma x  (C = 2B columns); Sigma^T x -> CG on Sigma^T Sigma -> Sigma z
+// out = P^Sigma x  (C = 2B columns); Sigma^T x -> CG on Sigma^T Sigma -> Sigma z.
+// The mixed path preconditions the FP64 CG with an FP32 dense (L + 11^T/N_f)^{-1}.
 void project_sigma(mot_handle* h, const Work& W, const double* x, double* out, cudaStream_t s) {
     const int C = 2 * h->B;
     launch_sigma_t(h, x, C, W.fvec, s);
-    launch_cg(h, h->Lf, nullptr, W.fvec, C, W.zvec, W.cgw, s);
+    if (h->d_Lfinvf && h->d_pcg_work && !h->precomputing)
+        h->last_pcg_iters = pcg_dense_prec(h, h->Lf, h->nfpd, h->d_Lfinvf, W.fvec, C, W.zvec, h->d_pcg_work,
+                                           h->d_pcg_scal, h->d_pcg_f32, h->opt.cg_tol, 50, s);
+    else
+        launch_cg(h, h->Lf, nullptr, W.fvec, C, W.zvec, W.cgw, s);
     launch_sigma(h, W.zvec, C, out, s);
 }
 
@@ -380,6 +388,14 @@ int ensure_state(mot_handle* h, int B) {
         h->d_win32 = (float*)dalloc(h, sizeof(float) * (size_t)(h->max_tail_lag + 1) * bv);
         h->d_xf = (float*)dalloc(h, sizeof(float) * 2 * bv);
         if (!h->d_ring32 || !h->d_win32 || !h->d_xf) return fail(h, MOT_EOOM, "device allocation of the march state");
+        if (h->d_Lfinvf) {
+            const size_t blk = (size_t)h->nfpd * 2 * B;
+            h->d_pcg_work = (double*)dalloc(h, sizeof(double) * (4 * blk + (size_t)((h->nfpd + 63) / 64) * 2 * B));
+            h->d_pcg_scal = (double*)dalloc(h, sizeof(double) * 8 * 2 * B);
+            h->d_pcg_f32 = (float*)dalloc(h, sizeof(float) * blk);
+            if (!h->d_pcg_work || !h->d_pcg_scal || !h->d_pcg_f32)
+                return fail(h, MOT_EOOM, "device allocation of the march state");
+        }
     }
     h->d_wprev1 = (double*)dalloc(h, sizeof(double) * bv);
     h->d_wprev2 = (double*)dalloc(h, sizeof(double) * bv);
@@ -416,10 +432,11 @@ void free_state(mot_handle* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->d_wprev1 = h->d_wprev2 = nullptr;
-    void* fptrs[] = {h->d_ring32, h->d_win32, h->d_xf};
+    void* fptrs[] = {h->d_ring32, h->d_win32, h->d_xf, h->d_pcg_work, h->d_pcg_scal, h->d_pcg_f32};
     for (void* p : fptrs)
         if (p) cudaFree(p);
-    h->d_ring32 = h->d_win32 = h->d_xf = nullptr;
+    h->d_ring32 = h->d_win32 = h->d_xf = h->d_pcg_f32 = nullptr;
+    h->d_pcg_work = h->d_pcg_scal = nullptr;
     h->d_waves = h->d_ring = h->d_win = h->d_cur = h->d_dft = h->d_work = h->d_partial = nullptr;
     h->d_V = h->d_H = h->d_g = h->d_cs = h->d_sn = h->d_red = h->d_resid = nullptr;
     h->d_gm_active = h->d_gm_jend = nullptr;
@@ -520,7 +537,9 @@ int do_step(mot_handle* h, cudaStream_t s) {
         // FP64 iterative refinement: r = b - Q_0 x with the FP64 dense Q_0,
         // correction from the reduced-precision GMRES, until |r| <= gmres_tol |b|
         const int gm_iters = h->last_gmres_iters;
-        for (int sweep = 0; sweep < 3; sweep++) {
+        // default: one FP64 residual and one correction (no residual re-check after it)
+        const int max_sweeps = h->opt.refine_sweeps > 0 ? h->opt.refine_sweeps : 1;
+        for (int sweep = 0; sweep < max_sweeps; sweep++) {
             apply_q0_dense64(h, W.x, W.r, s);
             launch_axpby(h, n, 1.0, W.b, -1.0, W.r, W.r, s);
             launch_gm_norm(h, W.r, W.nrm, s);
@@ -603,6 +622,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
         if (opt->cg_maxit > 0) h->opt.cg_maxit = opt->cg_maxit;
         h->opt.timing = opt->timing;
         h->opt.mixed_flags = opt->mixed_flags;
+        h->opt.refine_sweeps = opt->refine_sweeps;
     }
     auto bad = [&](const char* m) {
         h->err = m;
@@ -1074,6 +1094,32 @@ int precompute_mixed(mot_handle* h) {
         cudaFree(piv);
         h->device_bytes -= (int64_t)(2 * sizeof(double) * (size_t)n2 * n2 + sizeof(int) * (size_t)(n2 + 1));
     }
+    {
+        // preconditioner of the FP64 CG behind P^Sigma: (Sigma^T Sigma + 11^T/N_f)^{-1}, which is the
+        // pseudo-inverse on the range of the face Laplacian (connected surface), kept in FP32
+        const int npd = (h->nf + 63) / 64 * 64;
+        double* A = (double*)dalloc(h, sizeof(double) * (size_t)npd * npd);
+        double* inv = (double*)dalloc(h, sizeof(double) * (size_t)npd * npd);
+        int* piv = (int*)dalloc(h, sizeof(int) * (size_t)(npd + 1));
+        h->d_Lfinvf = (float*)dalloc(h, sizeof(float) * (size_t)npd * npd);
+        if (!A || !inv || !piv || !h->d_Lfinvf) return fail(h, MOT_EOOM, "device allocation (Laplacian factorisation)");
+        dense_lap_plus_j(h, h->Lf, npd, A, s);
+        const int bad = dense_lu(h, npd, A, piv, piv + npd, s);
+        if (bad == 0) {
+            dense_inverse_from_lu(h, npd, A, piv, inv, s);
+            launch_d2f(h, (size_t)npd * npd, inv, h->d_Lfinvf, s);
+            h->nfpd = npd;
+        }
+        CK(cudaDeviceSynchronize());
+        cudaFree(A);
+        cudaFree(inv);
+        cudaFree(piv);
+        h->device_bytes -= (int64_t)(2 * sizeof(double) * (size_t)npd * npd + sizeof(int) * (size_t)(npd + 1));
+        if (bad != 0) {  // not connected: keep the plain CG
+            cudaFree(h->d_Lfinvf);
+            h->d_Lfinvf = nullptr;
+        }
+    }
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     int it[2];
@@ -1386,7 +1432,7 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->Gt.col, h->Gt.val, h->d_T0s, h->d_T0h, h->d_rhs_x, h->d_rhs_wf, h->d_tiles,
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
                     h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
-                    h->d_LFf, h->d_Minvf};
+                    h->d_LFf, h->d_Minvf, h->d_Lfinvf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);

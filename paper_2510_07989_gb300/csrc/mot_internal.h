@@ -144,6 +144,12 @@ struct mot_handle {
     float* d_xf = nullptr;         // FP32 staging: [2 bv]
     float* d_Minvf = nullptr;      // FP32 Q_0^{-1} (GMRES preconditioner), (2 npad)^2
     bool prec_active = false;      // apply_q0 computes Q_0 M v
+    float* d_Lfinvf = nullptr;     // FP32 (Sigma^T Sigma + 11^T/N_f)^{-1}, nfpd x nfpd (CG preconditioner)
+    int nfpd = 0;                  // N_f padded to 64
+    double* d_pcg_work = nullptr;  // 5 x nfpd x 2B
+    double* d_pcg_scal = nullptr;  // 6 x 2B doubles + 2B ints
+    float* d_pcg_f32 = nullptr;    // nfpd x 2B
+    int last_pcg_iters = 0;
     bool precomputing = false;     // dense operators being assembled (use the product form)
     double gm_tol = 1e-12;         // relative tolerance of the GMRES solve in progress
     int refine_sweeps = 0;         // FP64 refinement sweeps used by the last step
