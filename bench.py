@@ -38,6 +38,7 @@ METRIC = "MOT RHS·steps/s, batched mixed vs FP64 plain on one GB300, at ≤1e-6
 WORKLOADS = {
     # name: (mesh builder, eps_r, c dt, B, assembly options)
     "torus64x24": (lambda MS: MS.torus(1.0, 0.3, 64, 24), 4.0, 0.1, 64, dict(nq=3, ntheta=3, nrad=3, far_plain=6)),
+    "torus32x12": (lambda MS: MS.torus(1.0, 0.3, 32, 12), 4.0, 0.1, 64, dict(nq=3, ntheta=3, nrad=3, far_plain=6)),
     "icosphere3": (lambda MS: MS.icosphere(3), 2.0, 0.5, 1, dict(nq=3, ntheta=3, nrad=3, far_plain=6)),
     "pr1": (lambda MS: MS.icosphere(1), 2.0, 0.2, 1, dict()),
 }
@@ -60,6 +61,22 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def reduce_max(values, world):
+    """Max over ranks of a list of floats (identity for one rank)."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def throughput(world, B, steps, ms):
+    """Whole-job RHS*steps/s: every rank marches its own B plane waves (weak
+    scaling, no data-path collective), timed by the slowest rank."""
+    return world * B * steps / (ms / 1e3)
 
 
 def make_workload(name, rank=0):
@@ -263,12 +280,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max, e2e_ms_max = float(t[0]), float(t[1])
-    value = world * B * args.steps / (ms_max / 1e3)
-    e2e_value = world * B * args.steps / (e2e_ms_max / 1e3)
+    ms_max, e2e_ms_max = reduce_max([ms, e2e_s * 1e3], world)
+    value = throughput(world, B, args.steps, ms_max)
+    e2e_value = throughput(world, B, args.steps, e2e_ms_max)
     if rank != 0:
         return
     peaks, how = measured_peaks()

@@ -57,6 +57,7 @@ class ProductSystem:
             keep = lag <= lim
             entry = dict(rows=r[keep].astype(np.int32), cols=c[keep].astype(np.int32), lag=lag[keep].astype(np.int32),
                          val=v[keep], typ=typ, interior=interior, uses=uses, tail=None)
+            entry["lag0"] = np.nonzero(entry["lag"] == 0)[0]
             if m.ta is not None:
                 tr = np.repeat(np.arange(ne), np.diff(m.rowptr))
                 ok = m.ta <= ops.kmax - 1
@@ -114,7 +115,7 @@ class ProductSystem:
         s = [np.zeros(ne), np.zeros(ne), np.zeros(ne), np.zeros(ne)]
         parts = (l, sg)
         for e in self.kinds:
-            idx = np.nonzero(e["lag"] == 0)[0]
+            idx = e["lag0"]
             for part, outi in e["uses"]:
                 P = parts[part]
                 cu = e["val"][idx] * P[e["cols"][idx]]

@@ -304,3 +304,13 @@ def test_rayleigh_limit_far_field():
     ref = w ** 2 * a ** 3 * (2 - 1) / (2 + 2) * np.abs(np.cos(th))
     assert np.abs(Eth - ref).max() < 0.05 * ref.max()
     assert np.abs(Eth - Eth[::-1]).max() < 0.02 * ref.max()
+
+
+def test_product_form_oracle_matches_dense(pr1_ops, pr1_system):
+    """The product-form oracle (used for meshes too large for dense Q_k) follows
+    the same definition: it reproduces the dense oracle on PR1 to 1e-10."""
+    from oracle import product as P
+    exc = MS.single_wave(pr1_ops.dt, 30, 60)
+    ref = O.march(pr1_system, exc, 60)
+    W = P.ProductSystem(pr1_ops).march(exc, 60)
+    assert np.abs(W - ref).max() < 1e-10 * np.abs(ref).max()
