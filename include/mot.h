@@ -69,13 +69,18 @@ typedef struct {
                               MOT_MIX_Q032:   FP32 dense Q_0 in the GMRES iterations
                               MOT_MIX_REFINE: FP64 iterative refinement of the Q_0 solve
                               MOT_MIX_PRECOND: right-preconditioned GMRES with an FP32
-                                 copy of Q_0^{-1} (LU with partial pivoting at load) */
+                                 copy of Q_0^{-1} (LU with partial pivoting at load)
+                              MOT_MIX_TC:     with MOT_MIX_HIST32 and 2B = 128 on an sm_100-family
+                                 GPU, the history contraction runs on the tensor cores
+                                 (tcgen05): FP32 tiles and coefficients split into three
+                                 bf16 slices each, FP32 accumulation, compensated sums */
     int32_t refine_sweeps; /* MOT_MIX_REFINE: FP64 residual + correction sweeps per step
                               (stops early once |r| <= gmres_tol |b|); default 1 */
 } mot_options;
 
 enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8, MOT_MIX_PRECOND = 16,
-       MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND };
+       MOT_MIX_TC = 32,
+       MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND | MOT_MIX_TC };
 
 /*
  * Lag-window sparse matrix (one family / medium of Section V-B):
@@ -162,6 +167,9 @@ typedef struct {
        [3] Q_0 GMRES solve, [4] FP64 refinement, [5] projector + ring update,
        [6] current recovery and Fourier sums */
     double phase_ms[8];
+    /* history kernel of the current batch: 0 FP64, 1 FP32 CUDA cores,
+       2 tensor cores (tcgen05, bf16 x 3 slices) */
+    int32_t hist_kernel;
 } mot_info;
 
 /*

@@ -378,6 +378,11 @@ void launch_history32(mot_handle* h, const TaskList& tl, const float* tiles, con
         }
         h->launches++;
     }
+    launch_history_reduce(h, tl, C2, out_s1, out_s2, s);
+}
+
+void launch_history_reduce(mot_handle* h, const TaskList& tl, int C2, double* out_s1, double* out_s2,
+                           cudaStream_t s) {
     k_hist_reduce2<<<h->nrb, 256, 0, s>>>(tl.chunk_ptr, h->d_partial, C2, out_s1, out_s2);
     h->launches++;
 }

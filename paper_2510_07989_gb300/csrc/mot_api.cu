@@ -384,10 +384,23 @@ int ensure_state(mot_handle* h, int B) {
     h->d_win = (double*)dalloc(h, sizeof(double) * (size_t)(h->max_tail_lag + 1) * bv);
     h->d_cur = (double*)dalloc(h, sizeof(double) * 4 * (size_t)h->npad * B);
     if (h->opt.precision == MOT_PREC_MIXED && !h->precomputing) {
-        h->d_ring32 = (float*)dalloc(h, sizeof(float) * (size_t)h->R * 6 * bv);
-        h->d_win32 = (float*)dalloc(h, sizeof(float) * (size_t)(h->max_tail_lag + 1) * bv);
+        int major = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
+        h->hist_tc = mflag(h, MOT_MIX_HIST32) && mflag(h, MOT_MIX_TC) && 2 * B == 128 && major == 10 &&
+                      history_tc_fits(h->npad) && h->hist_tc_list.packed;
+        if (h->hist_tc) {
+            h->d_ring16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)h->R * 6 * bv);
+            h->d_win16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)(h->max_tail_lag + 1) * 3 * bv);
+            if (!h->d_ring16 || !h->d_win16) return fail(h, MOT_EOOM, "device allocation of the march state");
+            CK(cudaMemset(h->d_ring16, 0, sizeof(uint16_t) * (size_t)h->R * 6 * bv));
+            CK(cudaMemset(h->d_win16, 0, sizeof(uint16_t) * (size_t)(h->max_tail_lag + 1) * 3 * bv));
+        } else {
+            h->d_ring32 = (float*)dalloc(h, sizeof(float) * (size_t)h->R * 6 * bv);
+            h->d_win32 = (float*)dalloc(h, sizeof(float) * (size_t)(h->max_tail_lag + 1) * bv);
+            if (!h->d_ring32 || !h->d_win32) return fail(h, MOT_EOOM, "device allocation of the march state");
+        }
         h->d_xf = (float*)dalloc(h, sizeof(float) * 2 * bv);
-        if (!h->d_ring32 || !h->d_win32 || !h->d_xf) return fail(h, MOT_EOOM, "device allocation of the march state");
+        if (!h->d_xf) return fail(h, MOT_EOOM, "device allocation of the march state");
         if (h->d_Lfinvf) {
             const size_t blk = (size_t)h->nfpd * 2 * B;
             h->d_pcg_work = (double*)dalloc(h, sizeof(double) * (4 * blk + (size_t)((h->nfpd + 63) / 64) * 2 * B));
@@ -403,7 +416,7 @@ int ensure_state(mot_handle* h, int B) {
     h->d_dft = (double*)dalloc(h, sizeof(double) * std::max(1, h->nfreq) * 4 * (size_t)h->npad * B * 2);
     h->work_bytes = sizeof(double) * work_doubles(h);
     h->d_work = (double*)dalloc(h, h->work_bytes);
-    int maxch = std::max(h->hist.nchunks, h->lag0.nchunks);
+    int maxch = std::max(std::max(h->hist.nchunks, h->lag0.nchunks), h->hist_tc_list.nchunks);
     h->partial_bytes = sizeof(double) * (size_t)std::max(1, maxch) * 2 * MOT_TILE * 2 * B;
     h->d_partial = (double*)dalloc(h, h->partial_bytes);
     h->d_V = (double*)dalloc(h, sizeof(double) * (size_t)(h->gm_m + 1) * bv);
@@ -432,10 +445,13 @@ void free_state(mot_handle* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->d_wprev1 = h->d_wprev2 = nullptr;
-    void* fptrs[] = {h->d_ring32, h->d_win32, h->d_xf, h->d_pcg_work, h->d_pcg_scal, h->d_pcg_f32};
+    void* fptrs[] = {h->d_ring32, h->d_win32, h->d_xf, h->d_pcg_work, h->d_pcg_scal, h->d_pcg_f32, h->d_ring16,
+                     h->d_win16};
     for (void* p : fptrs)
         if (p) cudaFree(p);
     h->d_ring32 = h->d_win32 = h->d_xf = h->d_pcg_f32 = nullptr;
+    h->d_ring16 = h->d_win16 = nullptr;
+    h->hist_tc = false;
     h->d_pcg_work = h->d_pcg_scal = nullptr;
     h->d_waves = h->d_ring = h->d_win = h->d_cur = h->d_dft = h->d_work = h->d_partial = nullptr;
     h->d_V = h->d_H = h->d_g = h->d_cs = h->d_sn = h->d_red = h->d_resid = nullptr;
@@ -484,7 +500,7 @@ int do_step(mot_handle* h, cudaStream_t s) {
     const long long i = h->step + 1;
     const int n = h->npad * 2 * h->B;
     const size_t bv = (size_t)n;
-    CK(cudaMemsetAsync(h->d_cg_iters, 0, 2 * sizeof(int), s));
+    CK(cudaMemsetAsync(h->d_cg_iters, 0, 3 * sizeof(int), s));
 #define PEV(k) \
     if (h->pev[0]) cudaEventRecord(h->pev[k], s)
     PEV(0);
@@ -494,7 +510,10 @@ int do_step(mot_handle* h, cudaStream_t s) {
     const bool h32 = mx && mflag(h, MOT_MIX_HIST32);
     if (i >= 2) {
         launch_window_sums(h, i, s);
-        if (h32) {
+        if (h->hist_tc) {
+            if (h->max_tail_lag >= 1) launch_split3(h, h->max_tail_lag + 1, h->d_win, h->d_win16, s);
+            launch_history_tc(h, h->hist_tc_list, i, W.s1, W.s2, s);
+        } else if (h32) {
             if (h->max_tail_lag >= 1) launch_d2f(h, (size_t)(h->max_tail_lag + 1) * bv, h->d_win, h->d_win32, s);
             launch_history32(h, h->hist, h->d_tiles32, h->d_ring32, h->d_win32, nullptr, 0, i, W.s1, W.s2, s);
         } else {
@@ -570,14 +589,17 @@ int do_step(mot_handle* h, cudaStream_t s) {
     const int slot = (int)(i % h->R);
     launch_variants(h, W.ell, h->d_ring + ((size_t)slot * 2 + 0) * 3 * bv, h->eta, h->etap, s);
     launch_variants(h, W.sig, h->d_ring + ((size_t)slot * 2 + 1) * 3 * bv, h->eta, h->etap, s);
-    if (mx) launch_d2f(h, 6 * bv, h->d_ring + (size_t)slot * 6 * bv, h->d_ring32 + (size_t)slot * 6 * bv, s);
+    if (h->hist_tc)
+        launch_split_ring(h, slot, s);
+    else if (mx)
+        launch_d2f(h, 6 * bv, h->d_ring + (size_t)slot * 6 * bv, h->d_ring32 + (size_t)slot * 6 * bv, s);
     PEV(6);
     h->step = i;
     launch_recover(h, i, s);
     PEV(7);
 #undef PEV
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(h->h_cg_iters, h->d_cg_iters, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(h->h_cg_iters, h->d_cg_iters, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h->pev[0]) {
         for (int k = 0; k < 7; k++) {
@@ -594,6 +616,10 @@ int do_step(mot_handle* h, cudaStream_t s) {
         h->ev_pending = false;
     }
     h->last_cg_iters = h->h_cg_iters[0];
+    if (h->h_cg_iters[2] != 0)
+        return fail(h, MOT_ECUDA,
+                    "tensor-core history: a pipeline wait ran out of time (code " + std::to_string(h->h_cg_iters[2]) +
+                        ")");
     if (h->h_cg_iters[1] > 0) return fail(h, MOT_ENOCONV, "a projector or Gram CG solve reached its iteration limit");
     return st;
 }
@@ -802,6 +828,77 @@ constexpr int NTK = 10;
 const int kMatKind[12] = {0, 2, 3, 5, 6, 8, 1, 2, 4, 5, 7, 8};
 const int kKindVariant[NTK] = {0, 1, 2, 0, 1, 2, 0, 1, 2, 2};
 const int kKindFamily[NTK] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3};  // 0 A, 1 Ah, 2 At, 3 tail
+
+// Task list of the tensor-core history kernel. The kernel gathers coefficient
+// rows of every lag it touches; to keep the rows of the lags in use resident
+// in L2, the list is cut into (lag range, row block) pieces ordered lag range
+// first, so the CTAs that run at the same time work on the same few lags.
+// Within a piece: output target, coefficient transform (variant; windowed
+// sums separately), lag, column block -- the kernel accumulates runs of equal
+// (output, transform) in one tensor-memory buffer.
+int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::vector<int>& rbs) {
+    const int nrb = h->nrb;
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->dev);
+    if (l2 <= 0) l2 = 64 << 20;
+    // bf16 slices of l and s of one lag for B = 64: 2 parts x 3 slices x npad x 128 x 2 bytes
+    const double lag_bytes = 2.0 * 3.0 * h->npad * 128.0 * 2.0;
+    const int kr = std::max(1, (int)(0.4 * l2 / lag_bytes));
+    auto xform = [](int code) { return (code & 3) == 2 ? 3 : (code >> 2) & 3; };
+    std::vector<int> order(tasks.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const HistTask &ta = tasks[a], &tb = tasks[b];
+        const int ra = (ta.k - 1) / kr, rbb = (tb.k - 1) / kr;
+        if (ra != rbb) return ra < rbb;
+        if (rbs[a] != rbs[b]) return rbs[a] < rbs[b];
+        const int oa = (ta.code >> 4) & 1, ob = (tb.code >> 4) & 1;
+        if (oa != ob) return oa < ob;
+        if (xform(ta.code) != xform(tb.code)) return xform(ta.code) < xform(tb.code);
+        if (ta.k != tb.k) return ta.k < tb.k;
+        return ta.cb < tb.cb;
+    });
+    const int cap = MOT_TC_CHUNK;  // tasks per chunk (staged in the CTA's shared memory)
+    std::vector<HistTask> sorted(tasks.size());
+    std::vector<HistChunk> chunks;
+    std::vector<std::vector<int>> per_rb(nrb);
+    size_t i = 0;
+    for (size_t j = 0; j < order.size(); j++) sorted[j] = tasks[order[j]];
+    while (i < order.size()) {
+        const int rb = rbs[order[i]], r = (sorted[i].k - 1) / kr;
+        size_t j = i;
+        while (j < order.size() && rbs[order[j]] == rb && (sorted[j].k - 1) / kr == r && (int)(j - i) < cap) j++;
+        per_rb[rb].push_back((int)chunks.size());
+        chunks.push_back(HistChunk{rb, (int)i, (int)(j - i)});
+        i = j;
+    }
+    std::vector<int> rptr(nrb + 1, 0), rch;
+    for (int rb = 0; rb < nrb; rb++) {
+        rptr[rb] = (int)rch.size();
+        rch.insert(rch.end(), per_rb[rb].begin(), per_rb[rb].end());
+    }
+    rptr[nrb] = (int)rch.size();
+    TaskList& tl = h->hist_tc_list;
+    tl.ntasks = (int)sorted.size();
+    tl.nchunks = (int)chunks.size();
+    std::vector<uint2> packed(sorted.size());
+    for (size_t t = 0; t < sorted.size(); t++) {
+        const HistTask& x = sorted[t];
+        if (x.cb > 0xFFFF || x.k > 0x3FF || x.code > 0x3F) return MOT_OK;  // outside the packed range: no tensor path
+        packed[t] = make_uint2((unsigned)x.tile, (unsigned)x.cb | ((unsigned)x.k << 16) | ((unsigned)x.code << 26));
+    }
+    tl.packed = (uint2*)dalloc(h, sizeof(uint2) * std::max<size_t>(1, packed.size()));
+    tl.chunks = (HistChunk*)dalloc(h, sizeof(HistChunk) * std::max<size_t>(1, chunks.size()));
+    tl.rb_ptr = (int*)dalloc(h, sizeof(int) * (nrb + 1));
+    tl.rb_chunks = (int*)dalloc(h, sizeof(int) * std::max<size_t>(1, rch.size()));
+    if (!tl.packed || !tl.chunks || !tl.rb_ptr || !tl.rb_chunks)
+        return fail(h, MOT_EOOM, "device allocation (tensor-core task list)");
+    if (!packed.empty()) CK(cudaMemcpy(tl.packed, packed.data(), sizeof(uint2) * packed.size(), cudaMemcpyHostToDevice));
+    if (!chunks.empty()) CK(cudaMemcpy(tl.chunks, chunks.data(), sizeof(HistChunk) * chunks.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(tl.rb_ptr, rptr.data(), sizeof(int) * (nrb + 1), cudaMemcpyHostToDevice));
+    if (!rch.empty()) CK(cudaMemcpy(tl.rb_chunks, rch.data(), sizeof(int) * rch.size(), cudaMemcpyHostToDevice));
+    return MOT_OK;
+}
 
 int build_tiles(mot_handle* h, const mot_operators* ops) {
     const int T = MOT_TILE;
@@ -1025,6 +1122,9 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
     int st;
     if ((st = make_list(th_hist, rb_hist, h->hist)) != MOT_OK) return st;
     if ((st = make_list(th_lag0, rb_lag0, h->lag0)) != MOT_OK) return st;
+    if (h->opt.precision == MOT_PREC_MIXED && (h->opt.mixed_flags & MOT_MIX_TC) &&
+        (st = make_tc_list(h, th_hist, rb_hist)) != MOT_OK)
+        return st;
     h->d_tiles = (double*)dalloc(h, sizeof(double) * std::max<size_t>(1, tiles.size()));
     if (!h->d_tiles) return fail(h, MOT_EOOM, "device allocation (history tiles)");
     if (!tiles.empty()) CK(cudaMemcpy(h->d_tiles, tiles.data(), sizeof(double) * tiles.size(), cudaMemcpyHostToDevice));
@@ -1380,6 +1480,12 @@ MOT_API int mot_load_state(mot_handle* h, const void* buf, size_t size) {
     CK(cudaMemcpy(h->d_wprev1, p, wp, cudaMemcpyHostToDevice));
     p += wp;
     CK(cudaMemcpy(h->d_wprev2, p, wp, cudaMemcpyHostToDevice));
+    // reduced-precision copies of the ring used by the mixed history kernels
+    if (h->hist_tc)
+        for (int slot = 0; slot < h->R; slot++) launch_split_ring(h, slot, 0);
+    else if (h->d_ring32)
+        launch_d2f(h, (size_t)h->R * 6 * bv, h->d_ring, h->d_ring32, 0);
+    CK(cudaDeviceSynchronize());
     h->step = hd.step;
     return MOT_OK;
 }
@@ -1409,6 +1515,7 @@ MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
     info->hist_timed_launches = h->timed_launches;
     info->hist_timed_ms = h->timed_ms;
     for (int k = 0; k < 8; k++) info->phase_ms[k] = h->phase_ms[k];
+    info->hist_kernel = h->hist_tc ? 2 : (h->opt.precision == MOT_PREC_MIXED && mflag(h, MOT_MIX_HIST32)) ? 1 : 0;
     return MOT_OK;
 }
 
@@ -1432,7 +1539,8 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->Gt.col, h->Gt.val, h->d_T0s, h->d_T0h, h->d_rhs_x, h->d_rhs_wf, h->d_tiles,
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
                     h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
-                    h->d_LFf, h->d_Minvf, h->d_Lfinvf};
+                    h->d_LFf, h->d_Minvf, h->d_Lfinvf, h->hist_tc_list.packed, h->hist_tc_list.chunks,
+                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);

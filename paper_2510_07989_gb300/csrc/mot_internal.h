@@ -12,6 +12,8 @@
 #define MOT_TILE 32
 // Largest batch of plane waves per handle.
 #define MOT_MAX_B 64
+// Tasks per CTA of the tensor-core history kernel (staged in shared memory).
+#define MOT_TC_CHUNK 1024
 // Size (doubles) of the fixed device array used by mot_fields_noalloc.
 #define MOT_NOALLOC_FIELD_DOUBLES 262144
 
@@ -50,6 +52,12 @@ struct TaskList {
     int ntasks = 0;
     int nchunks = 0;
     int* chunk_ptr = nullptr;  // [nrb+1] chunk range of each row block (device)
+    // lists whose chunks of one row block are not contiguous: the chunks of
+    // row block rb are rb_chunks[rb_ptr[rb] .. rb_ptr[rb+1]) (device)
+    int* rb_ptr = nullptr;
+    int* rb_chunks = nullptr;
+    // tensor-core list: tasks packed in 8 bytes, x = tile, y = cb | k << 16 | code << 26
+    uint2* packed = nullptr;
 };
 
 struct mot_handle {
@@ -84,6 +92,7 @@ struct mot_handle {
     int64_t ntiles = 0;
     double tile_fill = 0;
     TaskList hist, lag0;
+    TaskList hist_tc_list;  // tensor-core history: chunks = (lag range, row block) pieces, lag range major
     int max_tail_lag = 0;  // windows W_a needed for a in [1, max_tail_lag]
 
     // march state (allocated at the first step for a batch size B)
@@ -122,7 +131,8 @@ struct mot_handle {
     int* d_gm_active = nullptr;    // [B] GMRES system still iterating
     int* d_gm_jend = nullptr;      // [B] Krylov dimension reached
     double* d_gm_bnorm = nullptr;  // [B] |b|
-    int* d_cg_iters = nullptr;     // [0] max CG iterations, [1] non-converged solves
+    int* d_cg_iters = nullptr;     // [0] max CG iterations, [1] non-converged solves,
+                                   // [2] tensor-core history: code of a wait that ran out (0 = none)
     int* h_cg_iters = nullptr;     // pinned
     int last_gmres_iters = 0;
     double last_gmres_resid = 0;
@@ -137,6 +147,9 @@ struct mot_handle {
     float* d_tiles32 = nullptr;    // FP32 copy of the history tiles
     float* d_ring32 = nullptr;     // FP32 copy of the coefficient ring
     float* d_win32 = nullptr;      // FP32 windowed sums
+    uint16_t* d_ring16 = nullptr;  // tensor-core path: bf16 slices of l and s, [R][2 parts][3 slices][npad][2B]
+    uint16_t* d_win16 = nullptr;   // tensor-core path: bf16 slices of the windowed sums, [a][3 slices][npad][2B]
+    bool hist_tc = false;          // history contraction on the tensor cores (mixed path, 2B = 128)
     double* d_Q0 = nullptr;        // dense Q_0, (2 npad)^2, interleaved (edge, component) order, FP64
     float* d_Q0f = nullptr;        // FP32 copy
     double* d_LF = nullptr;        // dense [M1 | M2], npad x 2 npad, FP64
@@ -173,6 +186,18 @@ void* dalloc(mot_handle* h, size_t bytes);
 // history
 void launch_history(mot_handle* h, const TaskList& tl, const double* tiles, const double* ring, const double* win,
                     const double* kry, int mode, long long step_i, double* out_s1, double* out_s2, cudaStream_t s);
+
+// tensor-core history (mixed path, 2B = 128): tiles from d_tiles32, panels from d_ring16/d_win16
+void launch_history_tc(mot_handle* h, const TaskList& tl, long long step_i, double* out_s1, double* out_s2,
+                       cudaStream_t s);
+// sum of the chunk partial results of a history launch into out_s1 / out_s2
+void launch_history_reduce(mot_handle* h, const TaskList& tl, int C2, double* out_s1, double* out_s2,
+                           cudaStream_t s);
+// npanels FP64 panels of npad x 2B values -> three bf16 slices each
+void launch_split3(mot_handle* h, int npanels, const double* src, uint16_t* dst, cudaStream_t s);
+// bf16 slices of l and s of ring slot `slot` (from the FP64 ring's [-v, u] variant)
+void launch_split_ring(mot_handle* h, int slot, cudaStream_t s);
+bool history_tc_fits(int npad);  // the row block's column order fits in shared memory
 
 // block-vector helpers (rows npad, C columns)
 void launch_axpby(mot_handle* h, int n, double a, const double* x, double b, const double* y, double* z,

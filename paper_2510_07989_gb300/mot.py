@@ -17,8 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libmot.so")
 
 MOT_OK, MOT_EINVAL, MOT_EOOM, MOT_ENOCONV, MOT_ECUDA, MOT_ESTATE = 0, -1, -2, -3, -4, -5
 MOT_PREC_FP64, MOT_PREC_MIXED = 0, 1
-MOT_MIX_HIST32, MOT_MIX_LF32, MOT_MIX_Q032, MOT_MIX_REFINE, MOT_MIX_PRECOND = 1, 2, 4, 8, 16
-MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND
+MOT_MIX_HIST32, MOT_MIX_LF32, MOT_MIX_Q032, MOT_MIX_REFINE, MOT_MIX_PRECOND, MOT_MIX_TC = 1, 2, 4, 8, 16, 32
+MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND | MOT_MIX_TC
 _NAMES = {0: "MOT_OK", -1: "MOT_EINVAL", -2: "MOT_EOOM", -3: "MOT_ENOCONV", -4: "MOT_ECUDA", -5: "MOT_ESTATE"}
 
 
@@ -63,7 +63,8 @@ class mot_info(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("gpu_launches", ctypes.c_int64), ("tile_fill", ctypes.c_double),
                 ("tile_count", ctypes.c_int64), ("hist_flops_per_step", ctypes.c_double),
                 ("hist_bytes_per_step", ctypes.c_double), ("hist_timed_launches", ctypes.c_int64),
-                ("hist_timed_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8)]
+                ("hist_timed_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8),
+                ("hist_kernel", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -60,3 +60,52 @@ def test_mixed_ragged_batch_l2(M):
         errs.append(rel(W[:, b].reshape(n, -1), ref))
     print("mixed L2 B=3 max rel errs", ["%.3e" % e for e in errs])
     assert max(errs) < TOL_MIXED
+
+
+@pytest.fixture(scope="module")
+def torus_small():
+    """Torus 12 x 6 (216 edges: seven 32-edge row blocks, the last one ragged),
+    eps_r = 4, c dt = 0.1 (k_max = 52): many lags, several tiles per row block."""
+    ops = assemble(MS.torus(1.0, 0.3, 12, 6), 4.0, 1.0, 0.1)
+    return ops, O.build_system(ops)
+
+
+def test_tensor_core_history_matches_oracle(M, torus_small):
+    """B = 64 selects the tcgen05 history kernel (bf16 x 3 slices, FP32
+    accumulation, compensated sums); sampled columns against the FP64 oracle
+    over every step, and against the FP32 CUDA-core kernel on the same inputs."""
+    ops, S = torus_small
+    exc = MS.fibonacci_batch(64, ops.dt, w_steps=30, t0_steps=60)
+    n = 130
+    s_tc = M.Solver(ops, precision=M.MOT_PREC_MIXED)
+    W = s_tc.run(exc, n)
+    assert s_tc.info()["hist_kernel"] == 2
+    errs = []
+    for b in (0, 9, 33, 63):
+        ref = O.march(S, exc, n, b=b)
+        errs.append(rel(W[:, b].reshape(n, -1), ref))
+    print("tensor-core history, torus 12x6 B=64 max rel errs", ["%.3e" % e for e in errs])
+    assert max(errs) < TOL_MIXED
+    s_cc = M.Solver(ops, precision=M.MOT_PREC_MIXED, mixed_flags=M.MOT_MIX_DEFAULT & ~M.MOT_MIX_TC)
+    W_cc = s_cc.run(exc, n)
+    assert s_cc.info()["hist_kernel"] == 1
+    # the FP32 CUDA-core kernel sums its FP32 tile products in FP64 every four
+    # tiles; the tensor-core kernel's compensated sums are at least as accurate
+    errs_cc = [rel(W_cc[:, b].reshape(n, -1), O.march(S, exc, n, b=b)) for b in (0, 33)]
+    print("CUDA-core history, same columns", ["%.3e" % e for e in errs_cc])
+    assert max(errs[0], errs[2]) <= max(errs_cc)
+
+
+def test_mixed_save_load_state_resumes_exactly(M, torus_small):
+    """mot_save_state / mot_load_state on the mixed path (reduced-precision ring
+    copies rebuilt from the FP64 ring): the resumed run repeats the original."""
+    ops, _ = torus_small
+    exc = MS.fibonacci_batch(64, ops.dt, w_steps=30, t0_steps=60)
+    a = M.Solver(ops, precision=M.MOT_PREC_MIXED)
+    a.run(exc, 70, keep=False)
+    state = M.mot_save_state(a.h)
+    W1 = a.run(exc, 15)
+    b = M.Solver(ops, precision=M.MOT_PREC_MIXED)
+    M.mot_load_state(b.h, state)
+    W2 = b.run(exc, 15)
+    assert np.array_equal(W1, W2)
