@@ -9,16 +9,21 @@
 // is D[m][n] += sum_k P[m][k] X[n][k] with M = 128 (columns of the coefficient
 // panel), N = 32 (tile rows), K = 32 (tile columns).
 //
+// Every coefficient panel multiplies two tiles, one per output (s1, s2); a
+// task gathers the panel once and multiplies both (the missing one is a zero
+// tile).
+//
 // Precision: both operands are split into three bf16 slices, x = x0 + x1 + x2
 // (each slice the round-to-nearest residual of the previous ones; the products
-// of two bf16 values are exact in the FP32 accumulator). The three tile slices
-// are stacked along N, so per K-half the tensor core runs
-//   P0 x [X0; X1; X2] (N = 96) into TMEM columns [0, 96),
-//   P1 x [X0; X1]     (N = 64) into columns [32, 96),
-//   P2 x X0           (N = 32) into columns [64, 96):
-// column block 0 holds only P0 X0, block 1 the terms of relative size 2^-8
-// (P0 X1 + P1 X0), block 2 those of size 2^-16 (P0 X2 + P1 X1 + P2 X0); their
-// sum is P X - (P1 X2 + P2 X1 + P2 X2), a relative truncation of about 2^-26.
+// of two bf16 values are exact in the FP32 accumulator). With Y, Z the tiles
+// of s1 and s2, the six tile slices are stacked along N as [Y0 Z0 Y1 Z1 Y2 Z2]
+// (32 rows each), so per K-half the tensor core runs
+//   P0 x [Y0 Z0 Y1 Z1 Y2 Z2] (N = 192) into TMEM columns [0, 192),
+//   P1 x [Y0 Z0 Y1 Z1]       (N = 128) into columns [64, 192),
+//   P2 x [Y0 Z0]             (N = 64)  into columns [128, 192):
+// columns [0, 64) hold only P0 Y0 | P0 Z0, [64, 128) the terms of relative
+// size 2^-8, [128, 192) those of size 2^-16; per output the three blocks sum
+// to P Y - (P1 Y2 + P2 Y1 + P2 Y2), a relative truncation of about 2^-26.
 // The tensor core's FP32 accumulation rounds once per MMA at the scale of the
 // accumulator, so the large block sees only two additions per task; after
 // FGROUP tasks the epilogue warps fold the buffer into a compensated FP32 pair
@@ -34,19 +39,20 @@
 // addresses. The windowed sums of the constant K~ tail are kept in their
 // [-v, u] form and taken as they are.
 //
-// Data movement per task: the FP32 tile (4 KB, contiguous) by one bulk copy
+// Data movement per task: the tile's three bf16 slices, split once at set-up
+// and stored in the swizzled B layout (6 KB, contiguous), by one bulk copy
 // (cp.async.bulk, completion on an mbarrier); the coefficient rows, a gather
 // through the row block's column order, by 16-byte cp.async copies that place
-// every 16-byte piece straight into the MN-major core-matrix layout the MMA
-// reads; the tile is split into its bf16 slices in shared memory by the
-// converter warps.
+// every 16-byte piece straight into the swizzled MN-major A layout.
 //
-// Warp roles (352 threads, one CTA per SM):
-//   warps 0-3  gather: coefficient rows by cp.async (arrival on completion, so
-//              these warps never wait for their own copies) and the tile copy
-//   warp  4    TMEM allocation; lane 0 issues the MMAs
-//   warps 5-8  epilogue (TMEM -> registers, compensated sums, partial results)
-//   warps 9-10 converters: FP32 tile -> bf16 slices in the MMA layout
+// Warp roles (224 threads, one CTA per SM):
+//   warps 0-1  gather: coefficient rows by cp.async (each lane's arrival fires
+//              on completion of its copies, so the warps never wait for them)
+//              and the tile copy
+//   warp  2    TMEM allocation; lane 0 issues the MMAs
+//   warps 3-6  epilogue (TMEM -> registers, compensated sums, partial results)
+// Arrivals on a barrier are shared-memory atomics on one word: the epilogue
+// warps arrive once per warp, after a warp-level sync.
 // Every mbarrier wait is bounded in time; a wait that runs out raises the
 // CTA's abort flag and the global error word, every role stops issuing work,
 // copies in flight are waited for, and TMEM is released before the CTA exits.
@@ -60,18 +66,17 @@ namespace {
 
 constexpr int T = MOT_TILE;                 // 32
 constexpr int TC_M = 128;                   // 2B columns per coefficient panel
-constexpr int NB = 4;                       // TMEM accumulator buffers
-constexpr int BUFCOLS = 96;                 // TMEM columns per buffer (three 32-column blocks)
+constexpr int NB = 2;                       // TMEM accumulator buffers
+constexpr int BUFCOLS = 192;                // TMEM columns per buffer (three magnitudes x two outputs x 32)
 constexpr int TMEM_COLS = 512;              // allocation (power of two >= NB * BUFCOLS)
 constexpr int FGROUP = 2;                   // tasks per TMEM accumulation
 constexpr int A_SLICE = TC_M * T * 2;       // 8192 bytes: one bf16 slice of a 128 x 32 panel
 constexpr int B_SLICE = T * T * 2;          // 2048 bytes: one bf16 slice of a tile
 constexpr int STAGE_A = 3 * A_SLICE;        // 24576
-constexpr int STAGE_B = 3 * B_SLICE;        // 6144
-constexpr int STAGE_F = T * T * 4;          // 4096: FP32 tile as copied
-constexpr int STAGE = STAGE_A + STAGE_B + STAGE_F;  // 34816
-constexpr int NPROD = 128, NEPI = 128, NCONV = 64;
-constexpr int TC_THREADS = NPROD + 32 + NEPI + NCONV;
+constexpr int STAGE_B = 6 * B_SLICE;        // 12288: both tiles' slices, ordered X0 hi, X1 hi, X0 mid, X1 mid, X0 lo, X1 lo
+constexpr int STAGE = STAGE_A + STAGE_B;    // 36864
+constexpr int NPROD = 64, NEPI = 128;
+constexpr int TC_THREADS = NPROD + 32 + NEPI;  // 224: warps 0-1 gather, 2 MMA, 3-6 epilogue
 constexpr int TC_CHUNK = MOT_TC_CHUNK;      // tasks per CTA (staged in shared memory)
 constexpr size_t TC_SMEM_MAX = 227 * 1024;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // bound of every wait (2 s)
@@ -114,24 +119,30 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 
 // Bounded wait for the phase of the given parity. Returns false when the CTA
 // was told to abort or when the bound ran out (then it raises the abort flag
-// and records `code` in the global error word).
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                       int code) {
-    unsigned long long t0 = 0;
-    for (uint32_t it = 0;; it++) {
-        if (mbar_try(bar, parity)) return true;
-        if ((it & 63) == 63) {
-            if (*abort_flag) return false;
-            const unsigned long long now = gtimer();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > WAIT_NS) {
-                *abort_flag = 1;
-                atomicExch(err, code);
-                return false;
-            }
+// and records `code` in the global error word). The slow path (time bound,
+// abort flag) is out of line and entered only after many failed tries, so the
+// common case costs no call.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                            int code) {
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        for (int i = 0; i < 64; i++)
+            if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            atomicExch(err, code);
+            return false;
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code) {
+#pragma unroll 1
+    for (int i = 0; i < 4096; i++)
+        if (mbar_try(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, abort_flag, err, code);
 }
 
 // Wait used while shutting down after an abort: bounded, ignores the flag.
@@ -272,10 +283,11 @@ __device__ __forceinline__ void two_sum(float& s, float& c, float v) {
 
 __device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-// Packed task of the tensor-core list: x = tile, y = cb | k << 16 | code << 26.
-__device__ __forceinline__ int pk_cb(uint2 d) { return (int)(d.y & 0xFFFFu); }
-__device__ __forceinline__ int pk_k(uint2 d) { return (int)((d.y >> 16) & 0x3FFu); }
-__device__ __forceinline__ int pk_code(uint2 d) { return (int)(d.y >> 26); }
+// Merged task of the tensor-core list: x, y = tiles of s1 and s2 (the zero
+// tile if absent), z = cb | k << 16 | (part | variant << 2) << 26.
+__device__ __forceinline__ int pk_cb(uint4 d) { return (int)(d.z & 0xFFFFu); }
+__device__ __forceinline__ int pk_k(uint4 d) { return (int)((d.z >> 16) & 0x3FFu); }
+__device__ __forceinline__ int pk_code(uint4 d) { return (int)(d.z >> 26); }
 
 // Coefficient transform of a task: its variant for l and s, 3 for the
 // windowed sums (used as stored).
@@ -283,17 +295,18 @@ __device__ __forceinline__ int task_xform(int code) { return (code & 3) == 2 ? 3
 
 template <int NS>
 struct TcLayout {
-    static constexpr int NBARS = 4 * NS + 2 * NB + 1;  // + one barrier for the final MMA drain
+    static constexpr int NBARS = 3 * NS + 2 * NB + 1;  // + one barrier for the final MMA drain
     static constexpr size_t BARS = (size_t)NS * STAGE;
     static constexpr size_t SLOT = BARS + 8 * NBARS;        // TMEM address, abort flag
     static constexpr size_t DESC = SLOT + 16;               // TC_CHUNK packed tasks
-    static constexpr size_t COLS = DESC + 8 * TC_CHUNK;     // column order of the row block (uint16)
+    static constexpr size_t COLS = DESC + 16 * TC_CHUNK;    // column order of the row block (uint16)
     static size_t bytes(int npad) { return COLS + (((size_t)npad * 2 + 15) / 16) * 16 + 1024; }
 };
 
 template <int NS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_hist_tc(const uint2* __restrict__ tasks, const HistChunk* __restrict__ chunks, const float* __restrict__ tiles,
+    k_hist_tc(const uint4* __restrict__ tasks, const HistChunk* __restrict__ chunks,
+              const __nv_bfloat16* __restrict__ tiles16,
               const __nv_bfloat16* __restrict__ ring16, const __nv_bfloat16* __restrict__ win16, long long step_i,
               int R, int npad, const int* __restrict__ colidx, double eta, double etap, double* __restrict__ partial,
               int* __restrict__ err) {
@@ -305,15 +318,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t bar0 = sbase + (uint32_t)L::BARS;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::SLOT);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    uint2* sdesc = reinterpret_cast<uint2*>(smem + L::DESC);
+    uint4* sdesc = reinterpret_cast<uint4*>(smem + L::DESC);
     uint16_t* scol = reinterpret_cast<uint16_t*>(smem + L::COLS);
     auto FULL_A = [&](int s) { return bar0 + 8u * s; };            // coefficient rows landed
-    auto TFULL = [&](int s) { return bar0 + 8u * (NS + s); };      // FP32 tile landed
+    auto TFULL = [&](int s) { return bar0 + 8u * (NS + s); };      // tile slices landed
     auto EMPTY = [&](int s) { return bar0 + 8u * (2 * NS + s); };  // MMAs done with the stage
-    auto FULL_B = [&](int s) { return bar0 + 8u * (3 * NS + s); }; // bf16 tile slices written
-    auto ACCF = [&](int b) { return bar0 + 8u * (4 * NS + b); };
-    auto ACCE = [&](int b) { return bar0 + 8u * (4 * NS + NB + b); };
-    const uint32_t DRAIN = bar0 + 8u * (4 * NS + 2 * NB);
+    auto ACCF = [&](int b) { return bar0 + 8u * (3 * NS + b); };
+    auto ACCE = [&](int b) { return bar0 + 8u * (3 * NS + NB + b); };
+    const uint32_t DRAIN = bar0 + 8u * (3 * NS + 2 * NB);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const HistChunk ch = chunks[blockIdx.x];
@@ -327,17 +339,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(FULL_A(s), NPROD);
             mbar_init(TFULL(s), 1);
             mbar_init(EMPTY(s), 1);
-            mbar_init(FULL_B(s), NCONV);
         }
         for (int b = 0; b < NB; b++) {
             mbar_init(ACCF(b), 1);
-            mbar_init(ACCE(b), NEPI);
+            mbar_init(ACCE(b), NEPI / 32);
         }
         mbar_init(DRAIN, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
-    if (warp == 4) {
+    if (warp == 2) {
         tmem_alloc(su32(tmem_slot), TMEM_COLS);
         tmem_relinquish();
     }
@@ -346,15 +357,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < 4) {
+    if (warp < 2) {
         // ---------------- gather: coefficient rows and the tile copy ----------------
         const int t = tid;
         const int l8 = lane & 7, l3 = lane >> 3;
+        // this lane's 16-byte pieces: slices q = 0..2, row groups ro, column quads mq of
+        // its warp's half (mq = 2 warp + 0/1); destination offsets do not depend on the task
+        uint32_t dofs[4][2];
+#pragma unroll
+        for (int ro = 0; ro < 4; ro++)
+#pragma unroll
+            for (int h = 0; h < 2; h++) dofs[ro][h] = a_chunk(ro * 8 + l8, (2 * warp + h) * 4 + l3);
         int issued = 0;  // tasks whose copies were issued
         bool ok = true;
         const size_t pstride = (size_t)npad * TC_M;  // elements of one bf16 slice of one panel
         for (int ti = 0; ti < ntask; ti++) {
-            const uint2 d = sdesc[ti];
+            const uint4 d = sdesc[ti];
             const int cb = pk_cb(d), k = pk_k(d), code = pk_code(d);
             if (step_i - k < 1) continue;
             const int j = issued;
@@ -363,24 +381,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ok = false;
                 break;
             }
-            if (t == 0) {
-                mbar_expect_tx(TFULL(s), STAGE_F);
-                bulk_g2s(sbase + s * STAGE + STAGE_A + STAGE_B, tiles + (size_t)d.x * T * T, STAGE_F, TFULL(s));
+            if (t == 0) {  // slices in the order Y0 Z0 Y1 Z1 Y2 Z2
+                mbar_expect_tx(TFULL(s), STAGE_B);
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    bulk_g2s(sbase + s * STAGE + STAGE_A + (2 * q) * B_SLICE, tiles16 + ((size_t)d.x * 3 + q) * (T * T),
+                             B_SLICE, TFULL(s));
+                    bulk_g2s(sbase + s * STAGE + STAGE_A + (2 * q + 1) * B_SLICE,
+                             tiles16 + ((size_t)d.y * 3 + q) * (T * T), B_SLICE, TFULL(s));
+                }
             }
             const int part = code & 3, var = (code >> 2) & 3;
             const __nv_bfloat16* pan = part == 2 ? win16 + (size_t)k * 3 * pstride
                                                  : ring16 + (((size_t)((step_i - k) % R) * 2 + part) * 3) * pstride;
             const int swap = (part != 2 && var == 2) ? 8 : 0;  // [-v, u]: 64-column halves exchanged
-            int e[4];
-#pragma unroll
-            for (int ro = 0; ro < 4; ro++) e[ro] = scol[cb * T + ro * 8 + l8];
             const uint32_t adst = sbase + s * STAGE;
 #pragma unroll
-            for (int i = 0; i < 12; i++) {
-                const int c = warp * 12 + i;  // 16-byte piece set 0..47 of this task
-                const int q = c >> 4, ro = (c >> 2) & 3, mg = (c & 3) * 4 + l3;
-                cp_async16(adst + q * A_SLICE + a_chunk(ro * 8 + l8, mg),
-                           pan + (size_t)q * pstride + (size_t)e[ro] * TC_M + (mg ^ swap) * 8);
+            for (int ro = 0; ro < 4; ro++) {
+                const __nv_bfloat16* row = pan + (size_t)scol[cb * T + ro * 8 + l8] * TC_M;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const __nv_bfloat16* src = row + ((((2 * warp + h) * 4 + l3) ^ swap) * 8);
+#pragma unroll
+                    for (int q = 0; q < 3; q++) cp_async16(adst + q * A_SLICE + dofs[ro][h], src + (size_t)q * pstride);
+                }
             }
             // the stage's FULL_A arrival fires when these copies have landed
             cp_async_arrive_noinc(FULL_A(s));
@@ -390,48 +414,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!ok && t == 0)  // let the tile copies in flight land before the CTA exits
             for (int jj = issued > NS ? issued - NS : 0; jj < issued; jj++)
                 mbar_wait_drain(TFULL(jj % NS), (uint32_t)(jj / NS) & 1u);
-    } else if (warp >= 9) {
-        // ---------------- converters: FP32 tile -> three bf16 slices ----------------
-        const int ct = tid - (NPROD + 32 + NEPI);  // 0 .. NCONV-1
-        int j = 0;
-        for (int ti = 0; ti < ntask; ti++) {
-            if (step_i - pk_k(sdesc[ti]) < 1) continue;
-            const int s = j % NS;
-            if (!mbar_wait(TFULL(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 1)) break;
-            unsigned char* bst = smem + s * STAGE + STAGE_A;
-            const unsigned char* stf = bst + STAGE_B;
-#pragma unroll
-            for (int h2 = 0; h2 < 128 / NCONV; h2++) {
-                const int pp = ct + h2 * NCONV;
-                const int cr = (pp >> 5) * 8 + (pp & 7), ckc = (pp >> 3) & 3;  // tile row, 8-column group
-                const float4 x0 = *reinterpret_cast<const float4*>(stf + (cr * T + ckc * 8) * 4);
-                const float4 x1 = *reinterpret_cast<const float4*>(stf + (cr * T + ckc * 8) * 4 + 16);
-                const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-                __nv_bfloat16 a[8], b[8], c[8];
-#pragma unroll
-                for (int e = 0; e < 8; e++) split3(xv[e], a[e], b[e], c[e]);
-                unsigned char* bd = bst + b_chunk(cr, ckc);
-                *reinterpret_cast<uint4*>(bd) =
-                    make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7]));
-                *reinterpret_cast<uint4*>(bd + B_SLICE) =
-                    make_uint4(pack2(b[0], b[1]), pack2(b[2], b[3]), pack2(b[4], b[5]), pack2(b[6], b[7]));
-                *reinterpret_cast<uint4*>(bd + 2 * B_SLICE) =
-                    make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
-            }
-            fence_proxy_async();  // the slices are read by the tensor core (async proxy)
-            mbar_arrive(FULL_B(s));
-            j++;
-        }
-    } else if (warp == 4) {
+    } else if (warp == 2) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             int j = 0, g = -1, ing = 0, cur = -1;
             uint32_t dcol = 0;
             for (int ti = 0; ti < ntask; ti++) {
-                const uint2 d = sdesc[ti];
+                const uint4 d = sdesc[ti];
                 if (step_i - pk_k(d) < 1) continue;
-                const int code = pk_code(d);
-                const int key = ((code >> 4) & 1) | (task_xform(code) << 1);  // buffer key: output, transform
+                const int key = task_xform(pk_code(d));  // a buffer holds tasks of one coefficient transform
                 if (g < 0 || key != cur || ing == FGROUP) {
                     if (g >= 0) tc_commit(ACCF(g % NB));
                     g++;
@@ -444,7 +435,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 const int s = j % NS;
                 if (!mbar_wait(FULL_A(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 4)) break;
-                if (!mbar_wait(FULL_B(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 6)) break;
+                if (!mbar_wait(TFULL(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 6)) break;
                 fence_proxy_async();  // coefficient rows written by cp.async (generic proxy)
                 tc_fence_after();
                 const uint32_t a0 = sbase + s * STAGE, b0 = a0 + STAGE_A;
@@ -452,16 +443,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // B columns 16 kk .. (32 bytes into each 64-byte row)
 #pragma unroll
                 for (int kk = 0; kk < 2; kk++)
-                    mma_bf16(dcol, desc_a_sw128(a0 + kk * 2048), desc_b_sw64(b0 + kk * 32), idesc_bf16(96),
+                    mma_bf16(dcol, desc_a_sw128(a0 + kk * 2048), desc_b_sw64(b0 + kk * 32), idesc_bf16(192),
                              (ing > 0 || kk > 0) ? 1u : 0u);
 #pragma unroll
                 for (int kk = 0; kk < 2; kk++)
-                    mma_bf16(dcol + 32, desc_a_sw128(a0 + A_SLICE + kk * 2048), desc_b_sw64(b0 + kk * 32),
-                             idesc_bf16(64), 1u);
+                    mma_bf16(dcol + 64, desc_a_sw128(a0 + A_SLICE + kk * 2048), desc_b_sw64(b0 + kk * 32),
+                             idesc_bf16(128), 1u);
 #pragma unroll
                 for (int kk = 0; kk < 2; kk++)
-                    mma_bf16(dcol + 64, desc_a_sw128(a0 + 2 * A_SLICE + kk * 2048), desc_b_sw64(b0 + kk * 32),
-                             idesc_bf16(32), 1u);
+                    mma_bf16(dcol + 128, desc_a_sw128(a0 + 2 * A_SLICE + kk * 2048), desc_b_sw64(b0 + kk * 32),
+                             idesc_bf16(64), 1u);
                 tc_commit(EMPTY(s));
                 ing++;
                 j++;
@@ -479,64 +470,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int quarter = warp & 3;  // TMEM lanes [32 quarter, 32 quarter + 32)
         const int m = quarter * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-        float hs[32], hc[32];
+        float hs0[32], hc0[32], hs1[32], hc1[32];  // compensated sums of s1 and s2
 #pragma unroll
-        for (int n = 0; n < 32; n++) hs[n] = hc[n] = 0.f;
+        for (int n = 0; n < 32; n++) hs0[n] = hc0[n] = hs1[n] = hc1[n] = 0.f;
         // per-column scale of each coefficient transform (u columns m < 64, v columns m >= 64)
         const bool ucol = m < TC_M / 2;
         const float xs0 = ucol ? (float)eta : (float)(1.0 / eta), xs1 = ucol ? (float)etap : (float)(1.0 / etap),
                     xs2 = ucol ? -1.f : 1.f;
-        bool written0 = false, written1 = false;
-        double* pch = partial + (size_t)blockIdx.x * 2 * T * TC_M;
-        auto flush_out = [&](int o) {
-            const bool w = o ? written1 : written0;
-            double* p = pch + (size_t)o * T * TC_M + m;
+        // folds buffer b (transform key) into the sums of output o
+        auto fold = [&](uint32_t col, float c, float (&hs)[32], float (&hc)[32], bool release, int b) {
+            float va[32], vb[32];
+            tmem_ld32(col + 64, va);   // terms of relative size 2^-8
+            tmem_ld32(col + 128, vb);  // and 2^-16
+            tmem_wait_ld();
 #pragma unroll
-            for (int n = 0; n < 32; n++) {
-                const double v = (double)hs[n] + (double)hc[n];
-                p[(size_t)n * TC_M] = w ? p[(size_t)n * TC_M] + v : v;
-                hs[n] = hc[n] = 0.f;
+            for (int n = 0; n < 32; n++) hc[n] += c * (va[n] + vb[n]);
+            tmem_ld32(col, va);  // the leading products
+            tmem_wait_ld();
+            if (release) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ACCE(b));
             }
-            if (o)
-                written1 = true;
-            else
-                written0 = true;
+#pragma unroll
+            for (int n = 0; n < 32; n++) two_sum(hs[n], hc[n], c * va[n]);
         };
         auto drain = [&](int gg, int key) -> bool {
             const int b = gg % NB;
             if (!mbar_wait(ACCF(b), (uint32_t)(gg / NB) & 1u, abort_flag, err, 5)) return false;
             tc_fence_after();
             __syncwarp();
-            const int x = key >> 1;
-            const float c = x == 0 ? xs0 : x == 1 ? xs1 : x == 2 ? xs2 : 1.f;
-            float va[32], vb[32];
-            tmem_ld32(tl + (uint32_t)(b * BUFCOLS + 32), va);  // terms of relative size 2^-8
-            tmem_ld32(tl + (uint32_t)(b * BUFCOLS + 64), vb);  // and 2^-16
-            tmem_wait_ld();
-#pragma unroll
-            for (int n = 0; n < 32; n++) hc[n] += c * (va[n] + vb[n]);
-            tmem_ld32(tl + (uint32_t)(b * BUFCOLS), va);  // the leading products
-            tmem_wait_ld();
-            tc_fence_before();
-            mbar_arrive(ACCE(b));
-#pragma unroll
-            for (int n = 0; n < 32; n++) two_sum(hs[n], hc[n], c * va[n]);
+            const float c = key == 0 ? xs0 : key == 1 ? xs1 : key == 2 ? xs2 : 1.f;
+            const uint32_t col = tl + (uint32_t)(b * BUFCOLS);
+            fold(col, c, hs0, hc0, false, b);
+            fold(col + 32, c, hs1, hc1, true, b);
             return true;
         };
         int g = -1, ing = 0, cur = -1;
         bool ok = true;
         for (int ti = 0; ti < ntask && ok; ti++) {
-            const uint2 d = sdesc[ti];
+            const uint4 d = sdesc[ti];
             if (step_i - pk_k(d) < 1) continue;
-            const int code = pk_code(d);
-            const int key = ((code >> 4) & 1) | (task_xform(code) << 1);
+            const int key = task_xform(pk_code(d));
             if (g < 0 || key != cur || ing == FGROUP) {
-                if (g >= 0) {
-                    if (!drain(g, cur)) {
-                        ok = false;
-                        break;
-                    }
-                    if ((key & 1) != (cur & 1)) flush_out(cur & 1);
+                if (g >= 0 && !drain(g, cur)) {
+                    ok = false;
+                    break;
                 }
                 g++;
                 ing = 0;
@@ -544,13 +523,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             ing++;
         }
-        if (ok && g >= 0 && drain(g, cur)) flush_out(cur & 1);
-        if (!written0) flush_out(0);  // zeros for an output this chunk has no tile for
-        if (!written1) flush_out(1);
+        if (ok && g >= 0) drain(g, cur);
+        double* p0 = partial + (size_t)blockIdx.x * 2 * T * TC_M + m;
+        double* p1 = p0 + (size_t)T * TC_M;
+#pragma unroll
+        for (int n = 0; n < 32; n++) {
+            p0[(size_t)n * TC_M] = (double)hs0[n] + (double)hc0[n];
+            p1[(size_t)n * TC_M] = (double)hs1[n] + (double)hc1[n];
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == 2) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
     }
@@ -571,6 +555,29 @@ __global__ void k_split3(size_t n, int npanels, const double* __restrict__ src, 
         d[0] = a;
         d[n] = b;
         d[2 * n] = c;
+    }
+}
+
+// Tiles for the tensor-core kernel: each FP32 32 x 32 tile as three bf16
+// slices, already in the K-major 64-byte-swizzled layout of the MMA's B
+// operand (6 KB per tile, copied to shared memory as is). The split is exact:
+// hi + mid + lo reproduces the FP32 value.
+__global__ void k_split_tiles(long long ntiles, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+    const long long total = ntiles * T * 4;  // (tile, row, 8-column group)
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long t = i / (T * 4);
+        const int r = (int)(i - t * T * 4) >> 2, kc = (int)(i & 3);
+        const float* x = src + (size_t)t * T * T + r * T + kc * 8;
+        __nv_bfloat16 a[8], b[8], c[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) split3(x[e], a[e], b[e], c[e]);
+        unsigned char* d = reinterpret_cast<unsigned char*>(dst + (size_t)t * 3 * T * T) + b_chunk(r, kc);
+        *reinterpret_cast<uint4*>(d) = make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7]));
+        *reinterpret_cast<uint4*>(d + B_SLICE) =
+            make_uint4(pack2(b[0], b[1]), pack2(b[2], b[3]), pack2(b[4], b[5]), pack2(b[6], b[7]));
+        *reinterpret_cast<uint4*>(d + 2 * B_SLICE) =
+            make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]), pack2(c[6], c[7]));
     }
 }
 
@@ -620,6 +627,14 @@ __global__ void k_hist_reduce_idx(const int* __restrict__ rb_ptr, const int* __r
 
 namespace mot {
 
+void launch_split_tiles(mot_handle* h, cudaStream_t s) {
+    const long long total = h->ntiles * T * 4;
+    if (total == 0) return;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
+    k_split_tiles<<<blocks, 256, 0, s>>>(h->ntiles, h->d_tiles32, reinterpret_cast<__nv_bfloat16*>(h->d_tiles16));
+    h->launches++;
+}
+
 void launch_split_ring(mot_handle* h, int slot, cudaStream_t s) {
     const size_t bv = (size_t)h->npad * 2 * h->B;
     const int blocks = (int)std::min<size_t>((2 * bv + 255) / 256, 152 * 16);
@@ -662,23 +677,23 @@ void launch_history_tc(mot_handle* h, const TaskList& tl, long long step_i, doub
             cudaFuncSetAttribute(k_hist_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
             attr = true;
         }
-        const uint2* pt = reinterpret_cast<const uint2*>(tl.packed);
+        const uint4* pt = tl.packed;
         const auto* r16 = reinterpret_cast<const __nv_bfloat16*>(h->d_ring16);
         const auto* w16 = reinterpret_cast<const __nv_bfloat16*>(h->d_win16);
         switch (history_tc_stages(h->npad)) {
             case 6:
                 k_hist_tc<6><<<tl.nchunks, TC_THREADS, TcLayout<6>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, h->d_tiles32, r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
+                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
                     h->d_partial, h->d_cg_iters + 2);
                 break;
             case 5:
                 k_hist_tc<5><<<tl.nchunks, TC_THREADS, TcLayout<5>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, h->d_tiles32, r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
+                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
                     h->d_partial, h->d_cg_iters + 2);
                 break;
             default:
                 k_hist_tc<4><<<tl.nchunks, TC_THREADS, TcLayout<4>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, h->d_tiles32, r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
+                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
                     h->d_partial, h->d_cg_iters + 2);
         }
         if (timed) {

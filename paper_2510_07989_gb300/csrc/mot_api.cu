@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <tuple>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -388,6 +389,14 @@ int ensure_state(mot_handle* h, int B) {
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
         h->hist_tc = mflag(h, MOT_MIX_HIST32) && mflag(h, MOT_MIX_TC) && 2 * B == 128 && major == 10 &&
                       history_tc_fits(h->npad) && h->hist_tc_list.packed;
+        if (h->hist_tc && !h->d_tiles16) {  // operator data: kept until mot_destroy
+            // ntiles + 1 tiles: the last one stays zero (the missing partner of a merged task)
+            h->d_tiles16 =
+                (uint16_t*)dalloc(h, sizeof(uint16_t) * 3 * (size_t)(h->ntiles + 1) * MOT_TILE * MOT_TILE);
+            if (!h->d_tiles16) return fail(h, MOT_EOOM, "device allocation (tensor-core tiles)");
+            launch_split_tiles(h, 0);
+            CK(cudaDeviceSynchronize());
+        }
         if (h->hist_tc) {
             h->d_ring16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)h->R * 6 * bv);
             h->d_win16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)(h->max_tail_lag + 1) * 3 * bv);
@@ -829,13 +838,15 @@ const int kMatKind[12] = {0, 2, 3, 5, 6, 8, 1, 2, 4, 5, 7, 8};
 const int kKindVariant[NTK] = {0, 1, 2, 0, 1, 2, 0, 1, 2, 2};
 const int kKindFamily[NTK] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3};  // 0 A, 1 Ah, 2 At, 3 tail
 
-// Task list of the tensor-core history kernel. The kernel gathers coefficient
-// rows of every lag it touches; to keep the rows of the lags in use resident
-// in L2, the list is cut into (lag range, row block) pieces ordered lag range
-// first, so the CTAs that run at the same time work on the same few lags.
-// Within a piece: output target, coefficient transform (variant; windowed
-// sums separately), lag, column block -- the kernel accumulates runs of equal
-// (output, transform) in one tensor-memory buffer.
+// Task list of the tensor-core history kernel. Every coefficient panel
+// (part, variant, lag, column block) of a row block multiplies at most one
+// tile per output (A_k and A~_k on l, A_k and A^_k on s): the two are merged
+// into one task that gathers the panel once and multiplies both tiles, the
+// missing one replaced by a zero tile. To keep the rows of the lags in use
+// resident in L2, the list is cut into (lag range, row block) pieces ordered
+// lag range first, so the CTAs that run at the same time work on the same few
+// lags. Within a piece: coefficient transform (variant; windowed sums
+// separately), lag, column block.
 int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::vector<int>& rbs) {
     const int nrb = h->nrb;
     int l2 = 0;
@@ -845,29 +856,43 @@ int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::v
     const double lag_bytes = 2.0 * 3.0 * h->npad * 128.0 * 2.0;
     const int kr = std::max(1, (int)(0.4 * l2 / lag_bytes));
     auto xform = [](int code) { return (code & 3) == 2 ? 3 : (code >> 2) & 3; };
-    std::vector<int> order(tasks.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](int a, int b) {
-        const HistTask &ta = tasks[a], &tb = tasks[b];
-        const int ra = (ta.k - 1) / kr, rbb = (tb.k - 1) / kr;
+    const unsigned zt = (unsigned)h->ntiles;  // index of the zero tile
+    struct Merged {
+        int rb, cb, k, code;  // code = part | variant << 2
+        unsigned tile[2];
+    };
+    std::vector<size_t> ord(tasks.size());
+    std::iota(ord.begin(), ord.end(), (size_t)0);
+    auto mkey = [&](size_t t) {
+        return std::make_tuple(rbs[t], tasks[t].cb, tasks[t].k, tasks[t].code & 15);
+    };
+    std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return mkey(a) < mkey(b); });
+    std::vector<Merged> m;
+    m.reserve(tasks.size() / 2 + 16);
+    for (size_t q = 0; q < ord.size(); q++) {
+        const size_t t = ord[q];
+        const HistTask& x = tasks[t];
+        const int out = (x.code >> 4) & 1;
+        if (q == 0 || mkey(t) != mkey(ord[q - 1])) m.push_back(Merged{rbs[t], x.cb, x.k, x.code & 15, {zt, zt}});
+        if (m.back().tile[out] != zt) return MOT_OK;  // two tiles for one output and panel: no tensor path
+        m.back().tile[out] = (unsigned)x.tile;
+    }
+    std::sort(m.begin(), m.end(), [&](const Merged& a, const Merged& b) {
+        const int ra = (a.k - 1) / kr, rbb = (b.k - 1) / kr;
         if (ra != rbb) return ra < rbb;
-        if (rbs[a] != rbs[b]) return rbs[a] < rbs[b];
-        const int oa = (ta.code >> 4) & 1, ob = (tb.code >> 4) & 1;
-        if (oa != ob) return oa < ob;
-        if (xform(ta.code) != xform(tb.code)) return xform(ta.code) < xform(tb.code);
-        if (ta.k != tb.k) return ta.k < tb.k;
-        return ta.cb < tb.cb;
+        if (a.rb != b.rb) return a.rb < b.rb;
+        if (xform(a.code) != xform(b.code)) return xform(a.code) < xform(b.code);
+        if (a.k != b.k) return a.k < b.k;
+        return a.cb < b.cb;
     });
     const int cap = MOT_TC_CHUNK;  // tasks per chunk (staged in the CTA's shared memory)
-    std::vector<HistTask> sorted(tasks.size());
     std::vector<HistChunk> chunks;
     std::vector<std::vector<int>> per_rb(nrb);
     size_t i = 0;
-    for (size_t j = 0; j < order.size(); j++) sorted[j] = tasks[order[j]];
-    while (i < order.size()) {
-        const int rb = rbs[order[i]], r = (sorted[i].k - 1) / kr;
+    while (i < m.size()) {
+        const int rb = m[i].rb, r = (m[i].k - 1) / kr;
         size_t j = i;
-        while (j < order.size() && rbs[order[j]] == rb && (sorted[j].k - 1) / kr == r && (int)(j - i) < cap) j++;
+        while (j < m.size() && m[j].rb == rb && (m[j].k - 1) / kr == r && (int)(j - i) < cap) j++;
         per_rb[rb].push_back((int)chunks.size());
         chunks.push_back(HistChunk{rb, (int)i, (int)(j - i)});
         i = j;
@@ -878,22 +903,22 @@ int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::v
         rch.insert(rch.end(), per_rb[rb].begin(), per_rb[rb].end());
     }
     rptr[nrb] = (int)rch.size();
-    TaskList& tl = h->hist_tc_list;
-    tl.ntasks = (int)sorted.size();
-    tl.nchunks = (int)chunks.size();
-    std::vector<uint2> packed(sorted.size());
-    for (size_t t = 0; t < sorted.size(); t++) {
-        const HistTask& x = sorted[t];
-        if (x.cb > 0xFFFF || x.k > 0x3FF || x.code > 0x3F) return MOT_OK;  // outside the packed range: no tensor path
-        packed[t] = make_uint2((unsigned)x.tile, (unsigned)x.cb | ((unsigned)x.k << 16) | ((unsigned)x.code << 26));
+    std::vector<uint4> packed(m.size());
+    for (size_t t = 0; t < m.size(); t++) {
+        const Merged& x = m[t];
+        if (x.cb > 0xFFFF || x.k > 0x3FF) return MOT_OK;  // outside the packed range: no tensor path
+        packed[t] = make_uint4(x.tile[0], x.tile[1], (unsigned)x.cb | ((unsigned)x.k << 16) | ((unsigned)x.code << 26), 0u);
     }
-    tl.packed = (uint2*)dalloc(h, sizeof(uint2) * std::max<size_t>(1, packed.size()));
+    TaskList& tl = h->hist_tc_list;
+    tl.ntasks = (int)m.size();
+    tl.nchunks = (int)chunks.size();
+    tl.packed = (uint4*)dalloc(h, sizeof(uint4) * std::max<size_t>(1, packed.size()));
     tl.chunks = (HistChunk*)dalloc(h, sizeof(HistChunk) * std::max<size_t>(1, chunks.size()));
     tl.rb_ptr = (int*)dalloc(h, sizeof(int) * (nrb + 1));
     tl.rb_chunks = (int*)dalloc(h, sizeof(int) * std::max<size_t>(1, rch.size()));
     if (!tl.packed || !tl.chunks || !tl.rb_ptr || !tl.rb_chunks)
         return fail(h, MOT_EOOM, "device allocation (tensor-core task list)");
-    if (!packed.empty()) CK(cudaMemcpy(tl.packed, packed.data(), sizeof(uint2) * packed.size(), cudaMemcpyHostToDevice));
+    if (!packed.empty()) CK(cudaMemcpy(tl.packed, packed.data(), sizeof(uint4) * packed.size(), cudaMemcpyHostToDevice));
     if (!chunks.empty()) CK(cudaMemcpy(tl.chunks, chunks.data(), sizeof(HistChunk) * chunks.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(tl.rb_ptr, rptr.data(), sizeof(int) * (nrb + 1), cudaMemcpyHostToDevice));
     if (!rch.empty()) CK(cudaMemcpy(tl.rb_chunks, rch.data(), sizeof(int) * rch.size(), cudaMemcpyHostToDevice));
@@ -1540,7 +1565,7 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
                     h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
                     h->d_LFf, h->d_Minvf, h->d_Lfinvf, h->hist_tc_list.packed, h->hist_tc_list.chunks,
-                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks};
+                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);

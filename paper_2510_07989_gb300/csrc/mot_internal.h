@@ -56,8 +56,9 @@ struct TaskList {
     // row block rb are rb_chunks[rb_ptr[rb] .. rb_ptr[rb+1]) (device)
     int* rb_ptr = nullptr;
     int* rb_chunks = nullptr;
-    // tensor-core list: tasks packed in 8 bytes, x = tile, y = cb | k << 16 | code << 26
-    uint2* packed = nullptr;
+    // tensor-core list: merged tasks, x = tile for s1, y = tile for s2 (the
+    // zero tile if absent), z = cb | k << 16 | (part | variant << 2) << 26
+    uint4* packed = nullptr;
 };
 
 struct mot_handle {
@@ -145,6 +146,7 @@ struct mot_handle {
     double hist_nnz_unique = 0;  // nonzeros of the stored tiles used by the history list
     // mixed-precision path (MOT_PREC_MIXED)
     float* d_tiles32 = nullptr;    // FP32 copy of the history tiles
+    uint16_t* d_tiles16 = nullptr; // tensor-core path: the tiles as three bf16 slices in the MMA's B layout
     float* d_ring32 = nullptr;     // FP32 copy of the coefficient ring
     float* d_win32 = nullptr;      // FP32 windowed sums
     uint16_t* d_ring16 = nullptr;  // tensor-core path: bf16 slices of l and s, [R][2 parts][3 slices][npad][2B]
@@ -195,6 +197,8 @@ void launch_history_reduce(mot_handle* h, const TaskList& tl, int C2, double* ou
                            cudaStream_t s);
 // npanels FP64 panels of npad x 2B values -> three bf16 slices each
 void launch_split3(mot_handle* h, int npanels, const double* src, uint16_t* dst, cudaStream_t s);
+// bf16 slices of the FP32 tiles in the tensor core's B layout (d_tiles32 -> d_tiles16)
+void launch_split_tiles(mot_handle* h, cudaStream_t s);
 // bf16 slices of l and s of ring slot `slot` (from the FP64 ring's [-v, u] variant)
 void launch_split_ring(mot_handle* h, int slot, cudaStream_t s);
 bool history_tc_fits(int npad);  // the row block's column order fits in shared memory
