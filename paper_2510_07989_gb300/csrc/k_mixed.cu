@@ -3,6 +3,8 @@
 // -> FP64 GEMM for the precomputed Q_0 and left factors, and the load-time
 // helpers that assemble those dense matrices column by column from the FP64
 // product form.
+#include <algorithm>
+
 #include "mot_internal.h"
 
 namespace {
@@ -218,15 +220,19 @@ __global__ void k_hist_reduce2(const int* __restrict__ chunk_ptr, const double* 
 
 // Y[M][N] (double) = A[M][K] (float, row-major, lda = K) * X[K][N] (float).
 // 128 x 64 output tile per CTA, 8 x 4 outputs per thread; FP32 products summed
-// in FP32 over 128 consecutive k, then added into FP64 accumulators.
-constexpr int SG_M = 128, SG_N = 64, SG_K = 16;
-__global__ void __launch_bounds__(256) k_sgemm_d(int M, int N, int K, const float* __restrict__ A,
+// in FP32 over 128 consecutive k, then added into FP64 accumulators. K is split
+// over gridDim.z CTAs (each a multiple of 128 long), so that small-N products
+// fill the GPU; with more than one split each CTA writes its FP64 partial
+// result to W[z][M][N] and k_sgemm_reduce sums the splits in a fixed order.
+constexpr int SG_M = 128, SG_N = 64, SG_K = 16, SG_FLUSH = 128;
+__global__ void __launch_bounds__(256) k_sgemm_d(int M, int N, int K, int kchunk, const float* __restrict__ A,
                                                  const float* __restrict__ X, double* __restrict__ Y) {
-    __shared__ float sa[SG_K][SG_M + 4];
-    __shared__ float sx[SG_K][SG_N];
+    __shared__ float sa[2][SG_K][SG_M + 4];
+    __shared__ __align__(16) float sx[2][SG_K][SG_N];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads: 4 cols x 8 rows each
     const int row0 = blockIdx.x * SG_M, col0 = blockIdx.y * SG_N;
+    const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
     float acc[8][4];
     double dacc[8][4];
 #pragma unroll
@@ -236,34 +242,71 @@ __global__ void __launch_bounds__(256) k_sgemm_d(int M, int N, int K, const floa
             acc[i][j] = 0.f;
             dacc[i][j] = 0.0;
         }
-    int since = 0;
-    for (int k0 = 0; k0 < K; k0 += SG_K) {
-        for (int e = tid; e < SG_M * SG_K; e += 256) {
-            const int r = e / SG_K, k = e - r * SG_K;
-            const int gr = row0 + r, gk = k0 + k;
-            sa[k][r] = (gr < M && gk < K) ? A[(size_t)gr * K + gk] : 0.f;
+    // loader mapping: A tile 128 rows x 16 k = 512 float4 (2 per thread, along k);
+    // X tile 16 k x 64 cols = 256 float4 (1 per thread, along the columns)
+    const bool avec = (K & 3) == 0, xvec = (N & 3) == 0;
+    float4 ra[2], rx;
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = tid + h * 256, r = e >> 2, kq = (e & 3) * 4;
+            const int gr = row0 + r, gk = k0 + kq;
+            if (gr < M && avec && gk + 3 < kend) {
+                ra[h] = __ldg(reinterpret_cast<const float4*>(A + (size_t)gr * K + gk));
+            } else {
+                float v[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) v[q] = (gr < M && gk + q < kend) ? A[(size_t)gr * K + gk + q] : 0.f;
+                ra[h] = make_float4(v[0], v[1], v[2], v[3]);
+            }
         }
-        for (int e = tid; e < SG_K * SG_N; e += 256) {
-            const int k = e / SG_N, c = e - k * SG_N;
-            const int gk = k0 + k, gc = col0 + c;
-            sx[k][c] = (gk < K && gc < N) ? X[(size_t)gk * N + gc] : 0.f;
+        {
+            const int k = tid >> 4, c4 = (tid & 15) * 4;
+            const int gk = k0 + k, gc = col0 + c4;
+            if (gk < kend && xvec && gc + 3 < N) {
+                rx = __ldg(reinterpret_cast<const float4*>(X + (size_t)gk * N + gc));
+            } else {
+                float v[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) v[q] = (gk < kend && gc + q < N) ? X[(size_t)gk * N + gc + q] : 0.f;
+                rx = make_float4(v[0], v[1], v[2], v[3]);
+            }
         }
-        __syncthreads();
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = tid + h * 256, r = e >> 2, kq = (e & 3) * 4;
+            sa[buf][kq + 0][r] = ra[h].x;
+            sa[buf][kq + 1][r] = ra[h].y;
+            sa[buf][kq + 2][r] = ra[h].z;
+            sa[buf][kq + 3][r] = ra[h].w;
+        }
+        *reinterpret_cast<float4*>(&sx[buf][tid >> 4][(tid & 15) * 4]) = rx;
+    };
+    int buf = 0, since = 0;
+    if (kbeg < kend) {
+        load(kbeg);
+        store(0);
+    }
+    __syncthreads();
+    for (int k0 = kbeg; k0 < kend; k0 += SG_K) {
+        const bool more = k0 + SG_K < kend;
+        if (more) load(k0 + SG_K);  // next tile in flight while this one is used
 #pragma unroll
         for (int k = 0; k < SG_K; k++) {
-            float av[8], xv[4];
-#pragma unroll
-            for (int i = 0; i < 8; i++) av[i] = sa[k][ty * 8 + i];
-#pragma unroll
-            for (int j = 0; j < 4; j++) xv[j] = sx[k][tx * 4 + j];
+            const float4 a0 = *reinterpret_cast<const float4*>(&sa[buf][k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&sa[buf][k][ty * 8 + 4]);
+            const float4 xv = *reinterpret_cast<const float4*>(&sx[buf][k][tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float xw[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
             for (int i = 0; i < 8; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], xv[j], acc[i][j]);
+                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(av[i], xw[j], acc[i][j]);
         }
-        __syncthreads();
         since += SG_K;
-        if (since >= 128) {
+        if (since >= SG_FLUSH) {
             since = 0;
 #pragma unroll
             for (int i = 0; i < 8; i++)
@@ -273,7 +316,11 @@ __global__ void __launch_bounds__(256) k_sgemm_d(int M, int N, int K, const floa
                     acc[i][j] = 0.f;
                 }
         }
+        if (more) store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
     }
+    double* out = Y + (size_t)blockIdx.z * M * N;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const int r = row0 + ty * 8 + i;
@@ -281,8 +328,16 @@ __global__ void __launch_bounds__(256) k_sgemm_d(int M, int N, int K, const floa
 #pragma unroll
         for (int j = 0; j < 4; j++) {
             const int c = col0 + tx * 4 + j;
-            if (c < N) Y[(size_t)r * N + c] = dacc[i][j] + (double)acc[i][j];
+            if (c < N) out[(size_t)r * N + c] = dacc[i][j] + (double)acc[i][j];
         }
+    }
+}
+
+__global__ void k_sgemm_reduce(size_t n, int S, const double* __restrict__ W, double* __restrict__ Y) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int z = 0; z < S; z++) v += W[(size_t)z * n + i];
+        Y[i] = v;
     }
 }
 
@@ -388,9 +443,32 @@ void launch_history_reduce(mot_handle* h, const TaskList& tl, int C2, double* ou
 }
 
 void launch_sgemm_d(mot_handle* h, int M, int N, int K, const float* A, const float* X, double* Y, cudaStream_t s) {
-    dim3 grid((M + SG_M - 1) / SG_M, (N + SG_N - 1) / SG_N);
-    k_sgemm_d<<<grid, 256, 0, s>>>(M, N, K, A, X, Y);
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
+    const int tiles = ((M + SG_M - 1) / SG_M) * ((N + SG_N - 1) / SG_N);
+    // K splits: about four CTAs per SM, each split a multiple of the FP64 flush length
+    int S = std::max(1, std::min((4 * nsm + tiles - 1) / tiles, std::min(16, (K + SG_FLUSH - 1) / SG_FLUSH)));
+    const size_t need = (size_t)S * M * N * sizeof(double);
+    if (S > 1 && need > h->sgws_bytes) {
+        if (h->d_sgws) {
+            cudaFree(h->d_sgws);
+            h->device_bytes -= (int64_t)h->sgws_bytes;
+        }
+        h->sgws_bytes = 0;
+        h->d_sgws = (double*)dalloc(h, need);
+        if (h->d_sgws) h->sgws_bytes = need;
+    }
+    if (S > 1 && !h->d_sgws) S = 1;  // no workspace: one split
+    const int kchunk = ((K + S - 1) / S + SG_FLUSH - 1) / SG_FLUSH * SG_FLUSH;
+    S = (K + kchunk - 1) / kchunk;
+    dim3 grid((M + SG_M - 1) / SG_M, (N + SG_N - 1) / SG_N, S);
+    k_sgemm_d<<<grid, 256, 0, s>>>(M, N, K, kchunk, A, X, S > 1 ? h->d_sgws : Y);
     h->launches++;
+    if (S > 1) {
+        const size_t n = (size_t)M * N;
+        k_sgemm_reduce<<<(int)std::min<size_t>((n + 255) / 256, 4096), 256, 0, s>>>(n, S, h->d_sgws, Y);
+        h->launches++;
+    }
 }
 
 void launch_d2f(mot_handle* h, size_t n, const double* x, float* y, cudaStream_t s) {

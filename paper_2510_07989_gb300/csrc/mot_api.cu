@@ -1565,7 +1565,7 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
                     h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
                     h->d_LFf, h->d_Minvf, h->d_Lfinvf, h->hist_tc_list.packed, h->hist_tc_list.chunks,
-                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16};
+                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16, h->d_sgws};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);

@@ -157,6 +157,8 @@ struct mot_handle {
     double* d_LF = nullptr;        // dense [M1 | M2], npad x 2 npad, FP64
     float* d_LFf = nullptr;        // FP32 copy
     float* d_xf = nullptr;         // FP32 staging: [2 bv]
+    double* d_sgws = nullptr;      // split-K partial results of the FP32 dense products
+    size_t sgws_bytes = 0;
     float* d_Minvf = nullptr;      // FP32 Q_0^{-1} (GMRES preconditioner), (2 npad)^2
     bool prec_active = false;      // apply_q0 computes Q_0 M v
     float* d_Lfinvf = nullptr;     // FP32 (Sigma^T Sigma + 11^T/N_f)^{-1}, nfpd x nfpd (CG preconditioner)
