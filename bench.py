@@ -8,10 +8,12 @@ split into 3072 triangles (4608 edges, 9216 unknowns), eps_r = 4, c dt = 0.1
 directions and seeded polarisations, batched in one march.
 
 One bench step = one MOT step for the whole batch: right-hand side, full-depth
-history contraction over all lags, left preconditioner factors, GMRES solve of
-Q_0 with product-form matvecs, ring update, current recovery. Before timing,
-the march is advanced K+1 steps so every timed step contracts the full
-history (plus the W warm-up steps given on the command line).
+history contraction over all lags (tensor cores on the mixed path), left
+preconditioner factors, the Q_0 solve (mixed: right-preconditioned GMRES on
+the FP32 dense Q_0 with one FP64 refinement sweep; fp64: GMRES with product-
+form matvecs), ring update, current recovery. Before timing, the march is
+advanced K+1 steps so every timed step contracts the full history (plus the
+W warm-up steps given on the command line).
 
 Prints one JSON line (rank 0).
 """
@@ -144,6 +146,31 @@ class Clocks:
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# DRAM bytes (read + write) of one full-depth history launch, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel and
+# workload, with the SHA-1 of the kernel source they were taken on: a changed
+# source reports null until the counters are taken again.
+TRAFFIC = {}
+
+
+def kernel_source_sha(name):
+    import hashlib
+    p = os.path.join(ROOT, "paper_2510_07989_gb300", "csrc", name)
+    return hashlib.sha1(open(p, "rb").read()).hexdigest() if os.path.exists(p) else None
+
+
+def traffic_of(kernel, workload, source):
+    t = TRAFFIC.get((kernel, workload))
+    if t and t[1] == kernel_source_sha(source):
+        return t[0]
+    return None
+
+
+# issued tensor-core work of one history task: two K-halves of
+# 128 x (192 + 128 + 64) x 16 bf16 multiply-adds
+TC_FLOPS_PER_TASK = 2 * 2 * 128 * (192 + 128 + 64) * 16
 
 
 def measured_peaks():
@@ -289,27 +316,50 @@ def run_ours(args):
     hist_launches = info1["hist_timed_launches"] - info0["hist_timed_launches"]
     hist_ms = info1["hist_timed_ms"] - info0["hist_timed_ms"]
     flops = info1["hist_flops_per_step"]
-    if args.precision == "mixed":
-        peak, kname = 70.0, "k_hist_f32"  # FP32 FMA microbenchmark on this pool: 69.8-70.0 TFLOP/s
-        psrc = "FP32 CUDA-core FMA rate measured on this pool (152 SMs x 128 lanes x 2 x clock)"
+    hbytes = info1["hist_bytes_per_step"]
+    ms_l = hist_ms / hist_launches if hist_launches else None
+    kern = info1["hist_kernel"]
+    if kern == 2:
+        # tensor-core kernel: a sparse contraction streaming its tiles once per
+        # step; the roofline is HBM with the path's algorithmic bytes (FP32
+        # nonzeros of the lag matrices + the FP32 coefficients of every lag)
+        hbm = peaks.get("hbm_gbs")
+        achieved = hbytes / (ms_l / 1e3) / 1e9 if ms_l else None
+        tc_flops = info1["hist_tc_tasks"] * TC_FLOPS_PER_TASK
+        bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        roof = {"kernel": "k_hist_tc", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm if achieved else None,
+                "traffic": traffic_of("k_hist_tc", args.workload, "k_tc_hist.cu"),
+                "peak_source": f"measured copy bandwidth ({how})",
+                "algorithmic_bytes_per_launch": hbytes, "algorithmic_flops_per_launch": flops,
+                "tensor_issued_tflops": tc_flops / (ms_l / 1e3) / 1e12 if ms_l else None,
+                "tensor_frac_of_bf16_sustained": tc_flops / (ms_l / 1e3) / 1e12 / bf16 if ms_l and bf16 else None}
     else:
-        peak, kname = 1.25, "k_hist_f64"  # GB300 FP64 nominal; FMA microbenchmark on this pool: 1.198
-        psrc = "nominal FP64 rate of the profiling recipe (fp64 ALU bound)"
-    achieved = flops / (hist_ms / hist_launches / 1e3) / 1e12 if hist_launches else None
-    roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
-            "peak_source": psrc,
-            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": info1["hist_bytes_per_step"],
-            "launches_timed": hist_launches, "ms_per_launch": hist_ms / hist_launches if hist_launches else None,
-            "share_of_step": (hist_ms / hist_launches) / (ms_max / args.steps) if hist_launches else None}
+        if kern == 1:
+            peak, kname = 70.0, "k_hist_f32"  # FP32 FMA microbenchmark on this pool: 69.8-70.0 TFLOP/s
+            psrc = "FP32 CUDA-core FMA rate measured on this pool (152 SMs x 128 lanes x 2 x clock)"
+        else:
+            peak, kname = 1.25, "k_hist_f64"  # GB300 FP64 nominal; FMA microbenchmark on this pool: 1.198
+            psrc = "nominal FP64 rate of the profiling recipe (fp64 ALU bound)"
+        achieved = flops / (ms_l / 1e3) / 1e12 if ms_l else None
+        roof = {"kernel": kname, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None, "peak_source": psrc,
+                "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": hbytes}
+    roof.update({"launches_timed": hist_launches, "ms_per_launch": ms_l,
+                 "share_of_step": ms_l / (ms_max / args.steps) if ms_l else None})
     line = {"metric": METRIC, "value": value, "unit": "RHS·steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "ne": ops.ne, "unknowns": 2 * ops.ne, "eps_r": ops.eps_r,
                        "c_dt": ops.dt, "k_max": ops.kmax, "history_lags": K, "rhs_per_step": B,
-                       "precision": "mixed (FP32 history tiles, dense FP32 Q_0 and left factors, FP64 sums, FP64 CG projector)" if args.precision == "mixed" else "fp64 plain",
+                       "precision": ("mixed (history on tensor cores: FP32 tiles and coefficients as bf16 x 3, "
+                                     "compensated FP32 sums; FP32 dense Q_0 and Q_0^-1, FP64 left factor, "
+                                     "FP64 refinement, FP64 CG projector)" if kern == 2 else
+                                     "mixed (FP32 history tiles, dense FP32 Q_0 and left factors, FP64 sums, "
+                                     "FP64 CG projector)") if args.precision == "mixed" else "fp64 plain",
                        "history_prefill_steps": K + 1, "load_s": round(t_load, 1),
-                       "l2": "inputs larger than L2 (history tiles %.1f GB)" % (info1["tile_count"] * 8192 / 1e9),
+                       "l2": "inputs larger than L2 (history tiles read per step %.1f GB)" % (
+                           info1["tile_count"] * {2: 6144, 1: 4096, 0: 8192}[kern] / 1e9),
                        "assembly_s": round(t_asm, 1), "parallelism": f"replicas{world}",
                        "gmres_iters_last_step": info1["last_gmres_iters"],
                        "tile_fill": round(info1["tile_fill"], 3)},
@@ -321,7 +371,8 @@ def run_ours(args):
                                   for k, name in enumerate(["rhs", "history", "left_factor", "gmres", "refine",
                                                             "projector_ring", "recover"])},
             "roofline": roof,
-            "peaks": {"source": how, "hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops")}}
+            "peaks": {"source": how, "hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops"),
+                      "bf16_tflops_sustained": peaks.get("bf16_tflops_sustained")}}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ops, exc)
     print(json.dumps(line), flush=True)

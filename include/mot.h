@@ -155,7 +155,8 @@ typedef struct {
     int64_t tile_count;         /* stored history tiles (all lags and families) */
     /* algorithmic work of one full-depth history contraction (all lags live):
        2 flops per stored nonzero per right-hand-side column it multiplies,
-       and 8 bytes per stored nonzero plus the coefficient ring it reads */
+       and per stored nonzero plus per coefficient of the lags it reads one
+       value at the stored precision (8 bytes FP64, 4 bytes on the mixed path) */
     double hist_flops_per_step;
     double hist_bytes_per_step;
     /* with mot_options.timing: history-contraction launches (full depth, lags
@@ -170,6 +171,9 @@ typedef struct {
     /* history kernel of the current batch: 0 FP64, 1 FP32 CUDA cores,
        2 tensor cores (tcgen05, bf16 x 3 slices) */
     int32_t hist_kernel;
+    /* tensor-core history: tasks of one full-depth launch (each multiplies one
+       gathered 32 x 2B coefficient panel by two 32 x 32 tiles) */
+    int64_t hist_tc_tasks;
 } mot_info;
 
 /*

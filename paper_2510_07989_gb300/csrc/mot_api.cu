@@ -1536,7 +1536,10 @@ MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
     info->tile_count = h->ntiles;
     const double Bc = std::max(1, h->B);
     info->hist_flops_per_step = 2.0 * h->hist_nnz_tasks * 2.0 * Bc;
-    info->hist_bytes_per_step = 8.0 * h->hist_nnz_unique + 8.0 * (double)h->K * 2.0 * 2.0 * h->ne * Bc;
+    // values at the precision the path stores them: FP64, or FP32 on the mixed path
+    const double vb = h->opt.precision == MOT_PREC_MIXED ? 4.0 : 8.0;
+    info->hist_bytes_per_step = vb * h->hist_nnz_unique + vb * (double)h->K * 2.0 * 2.0 * h->ne * Bc;
+    info->hist_tc_tasks = h->hist_tc_list.ntasks;
     info->hist_timed_launches = h->timed_launches;
     info->hist_timed_ms = h->timed_ms;
     for (int k = 0; k < 8; k++) info->phase_ms[k] = h->phase_ms[k];

@@ -64,7 +64,7 @@ class mot_info(ctypes.Structure):
                 ("tile_count", ctypes.c_int64), ("hist_flops_per_step", ctypes.c_double),
                 ("hist_bytes_per_step", ctypes.c_double), ("hist_timed_launches", ctypes.c_int64),
                 ("hist_timed_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8),
-                ("hist_kernel", ctypes.c_int32)]
+                ("hist_kernel", ctypes.c_int32), ("hist_tc_tasks", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
