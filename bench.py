@@ -152,7 +152,13 @@ class Clocks:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel and
 # workload, with the SHA-1 of the kernel source they were taken on: a changed
 # source reports null until the counters are taken again.
-TRAFFIC = {}
+TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+    #     --clock-control none -k regex:k_hist_tc -s 56 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline
+    ("k_hist_tc", "torus64x24"): (47749068800 + 230510848, "4f02357985304f7f63f8fa1f4718af96ba79c41f"),
+    # the same on --workload torus32x12
+    ("k_hist_tc", "torus32x12"): (4477955328 + 17707008, "4f02357985304f7f63f8fa1f4718af96ba79c41f"),
+}
 
 
 def kernel_source_sha(name):
