@@ -73,14 +73,19 @@ typedef struct {
                               MOT_MIX_TC:     with MOT_MIX_HIST32 and 2B = 128 on an sm_100-family
                                  GPU, the history contraction runs on the tensor cores
                                  (tcgen05): FP32 tiles and coefficients split into three
-                                 bf16 slices each, FP32 accumulation, compensated sums */
+                                 bf16 slices each, FP32 accumulation, compensated sums
+                              MOT_MIX_EMU64:  on an sm_100-family GPU, the FP64 dense products
+                                 of the step (left factor, refinement residual) run on the
+                                 tensor cores as exact products of 7-bit integer slices
+                                 (relative error about 2^-40 of sum |A||x|) */
     int32_t refine_sweeps; /* MOT_MIX_REFINE: FP64 residual + correction sweeps per step
                               (stops early once |r| <= gmres_tol |b|); default 1 */
 } mot_options;
 
 enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8, MOT_MIX_PRECOND = 16,
-       MOT_MIX_TC = 32,
-       MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND | MOT_MIX_TC };
+       MOT_MIX_TC = 32, MOT_MIX_EMU64 = 64,
+       MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND | MOT_MIX_TC |
+                         MOT_MIX_EMU64 };
 
 /*
  * Lag-window sparse matrix (one family / medium of Section V-B):

@@ -269,7 +269,10 @@ bool mflag(const mot_handle* h, int bit) { return (h->opt.mixed_flags & bit) != 
 
 // out = Q_0 v with the dense FP64 Q_0 (the refinement residual of the mixed path)
 void apply_q0_dense64(mot_handle* h, const double* v, double* out, cudaStream_t s) {
-    launch_gemm_rect(h, 2 * h->npad, 2 * h->npad, h->d_Q0, v, h->B, out, s);
+    if (h->emu_Q0.a16)  // emulated FP64 on the tensor cores (MOT_MIX_EMU64)
+        launch_emu_gemm(h, h->emu_Q0, v, h->B, out, s);
+    else
+        launch_gemm_rect(h, 2 * h->npad, 2 * h->npad, h->d_Q0, v, h->B, out, s);
 }
 
 // out = Q_0 v: dense Q_0 (mixed path, FP32 or FP64 copy) or the FP64 product form
@@ -541,7 +544,10 @@ int do_step(mot_handle* h, cudaStream_t s) {
             launch_d2f(h, 2 * bv, W.y1, h->d_xf, s);
             launch_sgemm_d(h, h->npad, 2 * h->B, 2 * h->npad, h->d_LFf, h->d_xf, W.b, s);
         } else {
-            launch_gemm_rect(h, h->npad, 2 * h->npad, h->d_LF, W.y1, 2 * h->B, W.b, s);
+            if (h->emu_LF.a16)  // emulated FP64 on the tensor cores (MOT_MIX_EMU64)
+                launch_emu_gemm(h, h->emu_LF, W.y1, 2 * h->B, W.b, s);
+            else
+                launch_gemm_rect(h, h->npad, 2 * h->npad, h->d_LF, W.y1, 2 * h->B, W.b, s);
         }
     } else {
         left_factor(h, W, W.y1, W.y2, W.b, s);
@@ -1252,6 +1258,13 @@ int precompute_mixed(mot_handle* h) {
     free_state(h);
     h->precomputing = false;
     if (it[1] > 0) return fail(h, MOT_ENOCONV, "a CG solve did not converge while assembling the dense operators");
+    int major = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
+    if (mflag(h, MOT_MIX_EMU64) && major == 10) {  // slices of Q_0 and [M1 | M2] for the emulated FP64 products
+        if ((st = emu_prepare(h, h->d_Q0, 2 * h->npad, 2 * h->npad, &h->emu_Q0)) != MOT_OK) return st;
+        if ((st = emu_prepare(h, h->d_LF, h->npad, 2 * h->npad, &h->emu_LF)) != MOT_OK) return st;
+        CK(cudaDeviceSynchronize());
+    }
     if (h32) {  // the FP64 history tiles are no longer read
         cudaFree(h->d_tiles);
         h->device_bytes -= (int64_t)(sizeof(double) * (size_t)std::max<int64_t>(1, h->ntiles) * MOT_TILE * MOT_TILE);
@@ -1568,7 +1581,9 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
                     h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
                     h->d_LFf, h->d_Minvf, h->d_Lfinvf, h->hist_tc_list.packed, h->hist_tc_list.chunks,
-                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16, h->d_sgws};
+                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16, h->d_sgws, h->d_emuws};
+    emu_free(h, &h->emu_Q0);
+    emu_free(h, &h->emu_LF);
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);

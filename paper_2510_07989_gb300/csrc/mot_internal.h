@@ -36,6 +36,15 @@ struct HistChunk {
     int count;
 };
 
+// Fixed FP64 matrix prepared for the emulated FP64 products on tensor cores:
+// six bf16 integer slices per value (rows scaled by 2^-ea), pre-arranged in
+// the MMA's layout, [Mp / 128][K / 32][6][128 x 32].
+struct EmuMat {
+    int M = 0, K = 0, Mp = 0;
+    int* ea = nullptr;        // [Mp] row exponents
+    uint16_t* a16 = nullptr;  // slices
+};
+
 // Device CSR matrix.
 struct DCsr {
     int n = 0, m = 0;
@@ -159,6 +168,9 @@ struct mot_handle {
     float* d_xf = nullptr;         // FP32 staging: [2 bv]
     double* d_sgws = nullptr;      // split-K partial results of the FP32 dense products
     size_t sgws_bytes = 0;
+    EmuMat emu_Q0, emu_LF;         // Q_0 and [M1 | M2] for the emulated FP64 products (MOT_MIX_EMU64)
+    unsigned char* d_emuws = nullptr;  // their per-call workspace (X slices, split-K partials)
+    size_t emuws_bytes = 0;
     float* d_Minvf = nullptr;      // FP32 Q_0^{-1} (GMRES preconditioner), (2 npad)^2
     bool prec_active = false;      // apply_q0 computes Q_0 M v
     float* d_Lfinvf = nullptr;     // FP32 (Sigma^T Sigma + 11^T/N_f)^{-1}, nfpd x nfpd (CG preconditioner)
@@ -204,6 +216,12 @@ void launch_split_tiles(mot_handle* h, cudaStream_t s);
 // bf16 slices of l and s of ring slot `slot` (from the FP64 ring's [-v, u] variant)
 void launch_split_ring(mot_handle* h, int slot, cudaStream_t s);
 bool history_tc_fits(int npad);  // the row block's column order fits in shared memory
+
+// emulated FP64 products on tensor cores (k_emu64.cu): Y (M x N) = A X with A
+// prepared once by emu_prepare from the device FP64 matrix A (M x K, ld K)
+int emu_prepare(mot_handle* h, const double* A, int M, int K, EmuMat* out);
+void emu_free(mot_handle* h, EmuMat* m);
+int launch_emu_gemm(mot_handle* h, const EmuMat& A, const double* X, int N, double* Y, cudaStream_t s);
 
 // block-vector helpers (rows npad, C columns)
 void launch_axpby(mot_handle* h, int n, double a, const double* x, double b, const double* y, double* z,

@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(_HERE, "libmot.so")
 
 MOT_OK, MOT_EINVAL, MOT_EOOM, MOT_ENOCONV, MOT_ECUDA, MOT_ESTATE = 0, -1, -2, -3, -4, -5
 MOT_PREC_FP64, MOT_PREC_MIXED = 0, 1
-MOT_MIX_HIST32, MOT_MIX_LF32, MOT_MIX_Q032, MOT_MIX_REFINE, MOT_MIX_PRECOND, MOT_MIX_TC = 1, 2, 4, 8, 16, 32
-MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND | MOT_MIX_TC
+MOT_MIX_HIST32, MOT_MIX_LF32, MOT_MIX_Q032, MOT_MIX_REFINE, MOT_MIX_PRECOND = 1, 2, 4, 8, 16
+MOT_MIX_TC, MOT_MIX_EMU64 = 32, 64
+MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND | MOT_MIX_TC | MOT_MIX_EMU64
 _NAMES = {0: "MOT_OK", -1: "MOT_EINVAL", -2: "MOT_EOOM", -3: "MOT_ENOCONV", -4: "MOT_ECUDA", -5: "MOT_ESTATE"}
 
 
