@@ -3,21 +3,22 @@
 // (the left factor [M1 | M2], Q_0) and X a K x N FP64 block vector.
 //
 // Every row of A is scaled by a power of two so that |A_ik| < 1, every column
-// of X likewise; each scaled value is split into six signed 7-bit integer
+// of X likewise; each scaled value is split into S signed 7-bit integer
 // slices, a = sum_p a_p 2^(-6 - 7(p-1)), |a_p| <= 64, held exactly in bf16.
 // The product of two slices is an integer of magnitude <= 2^12, exact in the
-// tensor core's FP32 accumulator; slices pairs are accumulated by weight
-// level L = p + q - 2 (pairs with p + q <= 7, six levels, 21 pairs), over K
-// chunks of 128, so that every partial sum stays an integer below 2^22 and the
-// FP32 accumulation is exact. After each chunk the epilogue folds the six
-// levels, scaled by 2^(-7L) (exact), into a compensated FP32 pair per output
-// element; the result is scaled back in FP64. The dropped levels (p + q >= 8)
-// and the slice representation leave a relative error of about 2^-40 of
-// sum_k |A_ik| |X_kj|.
+// tensor core's FP32 accumulator; slice pairs are accumulated by weight
+// level L = p + q - 2 (pairs with p + q <= S + 1: S levels), over K chunks of
+// 128, so that every partial sum stays an integer below 2^22 and the FP32
+// accumulation is exact. After each chunk the epilogue folds the S levels,
+// scaled by 2^(-7L) (exact), into a compensated FP32 pair per output element;
+// the result is scaled back in FP64. The dropped levels and the slice
+// representation leave a relative error of about 2^(-7S + 2) of
+// sum_k |A_ik| |X_kj|: S = 6 (21 pairs) for FP64-accurate products, S = 4
+// (10 pairs, ~2^-26) for the products the FP32 solves need.
 //
 // Slices are stacked along N so that one MMA covers a whole row of the
-// product table: A_p x [X_1; ...; X_(7-p)] (N = 64 (7 - p)) into TMEM columns
-// [64 (p-1), 384), i.e. level p + q - 2 of every q. Operands are pre-arranged
+// product table: A_p x [X_1; ...; X_(S+1-p)] (N = 64 (S + 1 - p)) into TMEM
+// columns [64 (p-1), 64 S), i.e. level p + q - 2 of every q. Operands are pre-arranged
 // in the K-major 64-byte-swizzled layout (rows of 32 bf16), A once at set-up
 // and X per call, so one bulk copy per operand moves a pipeline stage.
 //
@@ -39,33 +40,36 @@ using namespace tcx;
 constexpr int EM = 128;           // rows of A per CTA
 constexpr int EN = 64;            // columns of X per CTA
 constexpr int EK = 32;            // K per pipeline stage (one 64-byte row of bf16)
-constexpr int NSL = 6;            // slices per operand
-constexpr int NLEV = 6;           // weight levels kept (p + q <= 7)
 constexpr int KC_TILES = 4;       // stages per exact accumulation chunk (K = 128)
 constexpr int A_TILE = EM * EK * 2;          // 8192 bytes per slice
 constexpr int B_TILE = EN * EK * 2;          // 4096 bytes per slice
-constexpr int A_STAGE = NSL * A_TILE;        // 49152
-constexpr int B_STAGE = NSL * B_TILE;        // 24576
-constexpr int E_STAGE = A_STAGE + B_STAGE;   // 73728
-constexpr int E_NS = 3;                      // pipeline stages
 constexpr int E_THREADS = 192;
-constexpr int E_TMEM = 512;                  // >= NLEV * EN
-constexpr int E_NBARS = 2 * E_NS + 3;        // FULL, EMPTY, ACCF, ACCE, DRAIN
-constexpr size_t E_SMEM = (size_t)E_NS * E_STAGE + 8 * E_NBARS + 16 + 1024;
+constexpr int E_TMEM = 512;                  // >= 64 S
 
-static_assert(NLEV * EN <= E_TMEM, "TMEM");
-static_assert(E_STAGE % 1024 == 0, "stage alignment");
-static_assert(E_SMEM <= 227 * 1024, "shared memory");
+// layout of the S-slice variant
+template <int S>
+struct EmuCfg {
+    static constexpr int A_STAGE = S * A_TILE;
+    static constexpr int B_STAGE = S * B_TILE;
+    static constexpr int STAGE = A_STAGE + B_STAGE;
+    static constexpr int NS = (int)((227 * 1024 - 2048) / STAGE);  // pipeline stages
+    static constexpr int NBARS = 2 * NS + 3;                        // FULL, EMPTY, ACCF, ACCE, DRAIN
+    static constexpr size_t SMEM = (size_t)NS * STAGE + 8 * NBARS + 16 + 1024;
+    static_assert(S * EN <= E_TMEM, "TMEM");
+    static_assert(STAGE % 1024 == 0, "stage alignment");
+    static_assert(SMEM <= 227 * 1024 && NS >= 2, "shared memory");
+};
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// six signed 7-bit slices of a (|a| < 1): a = sum_p s[p] 2^(-6 - 7p)
-__device__ __forceinline__ void slice6(double a, float (&s)[NSL]) {
+// S signed 7-bit slices of a (|a| < 1): a = sum_p s[p] 2^(-6 - 7p)
+template <int S>
+__device__ __forceinline__ void slice_n(double a, float (&s)[S]) {
     double t = a * 64.0;
 #pragma unroll
-    for (int p = 0; p < NSL; p++) {
+    for (int p = 0; p < S; p++) {
         const double r = rint(t);
         s[p] = (float)r;
         t = (t - r) * 128.0;
@@ -100,7 +104,8 @@ __global__ void k_row_exponents(int M, int Mp, int K, const double* __restrict__
     }
 }
 
-// A (M x K, row-major) -> slices in [Mp / 128][K / 32][6][128 x 32, 64-byte swizzle]
+// A (M x K, row-major) -> slices in [Mp / 128][K / 32][S][128 x 32, 64-byte swizzle]
+template <int NSL>
 __global__ void k_slice_rows(int M, int Mp, int K, const double* __restrict__ A, const int* __restrict__ ea,
                              __nv_bfloat16* __restrict__ A16) {
     const int KT = K / EK;
@@ -112,7 +117,7 @@ __global__ void k_slice_rows(int M, int Mp, int K, const double* __restrict__ A,
 #pragma unroll
         for (int e = 0; e < 8; e++) {
             const double a = i < M ? ldexp(A[(size_t)i * K + k8 * 8 + e], -ea[i]) : 0.0;
-            slice6(a, s[e]);
+            slice_n<NSL>(a, s[e]);
         }
         const int mt = i / EM, r = i % EM, kt = (k8 * 8) / EK, kc = ((k8 * 8) % EK) / 8;
         unsigned char* base = reinterpret_cast<unsigned char*>(A16 + (((size_t)mt * KT + kt) * NSL) * (EM * EK));
@@ -146,7 +151,8 @@ __global__ void k_col_exponents(int K, int N, const double* __restrict__ X, int*
     }
 }
 
-// X (K x N) -> slices of X^T in [NH][K / 32][6][64 x 32, 64-byte swizzle]
+// X (K x N) -> slices of X^T in [NH][K / 32][S][64 x 32, 64-byte swizzle]
+template <int NSL>
 __global__ void k_slice_cols(int K, int N, int NH, const double* __restrict__ X, const int* __restrict__ ex,
                              __nv_bfloat16* __restrict__ X16) {
     const int KT = K / EK;
@@ -158,7 +164,7 @@ __global__ void k_slice_cols(int K, int N, int NH, const double* __restrict__ X,
 #pragma unroll
         for (int e = 0; e < 8; e++) {
             const double x = n < N ? ldexp(X[(size_t)(k8 * 8 + e) * N + n], -ex[n]) : 0.0;
-            slice6(x, s[e]);
+            slice_n<NSL>(x, s[e]);
         }
         const int nh = n / EN, r = n % EN, kt = (k8 * 8) / EK, kc = ((k8 * 8) % EK) / 8;
         unsigned char* base = reinterpret_cast<unsigned char*>(X16 + (((size_t)nh * KT + kt) * NSL) * (EN * EK));
@@ -176,15 +182,19 @@ __global__ void k_slice_cols(int K, int N, int NH, const double* __restrict__ X,
 // Y[z] (M x N, rows < M, columns < N) = partial product over the k-tiles
 // [z * kts, (z + 1) * kts) of CTA split z (gridDim.z splits; kts a multiple
 // of KC_TILES).
+template <int NSL>
 __global__ void __launch_bounds__(E_THREADS, 1)
     k_emu_gemm(int M, int N, int K, int kts, const __nv_bfloat16* __restrict__ A16, const int* __restrict__ ea,
                const __nv_bfloat16* __restrict__ X16, const int* __restrict__ ex, double* __restrict__ Y,
                int* __restrict__ err) {
+    using C = EmuCfg<NSL>;
+    constexpr int E_NS = C::NS, E_STAGE = C::STAGE, A_STAGE = C::A_STAGE, B_STAGE = C::B_STAGE;
+    constexpr int NLEV = NSL;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = su32(smem);
     const uint32_t bar0 = sbase + E_NS * E_STAGE;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + E_NS * E_STAGE + 8 * E_NBARS);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + E_NS * E_STAGE + 8 * C::NBARS);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     auto FULL = [&](int s) { return bar0 + 8u * s; };
     auto EMPTY = [&](int s) { return bar0 + 8u * (E_NS + s); };
@@ -253,7 +263,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
                 for (int kk = 0; kk < 2; kk++) {
 #pragma unroll
                     for (int p = 1; p <= NSL; p++) {
-                        const int rows = EN * (7 - p);  // X slices 1 .. 7 - p stacked
+                        const int rows = EN * (NSL + 1 - p);  // X slices 1 .. S + 1 - p stacked
                         const uint64_t ad = desc_kmajor_sw64(a0 + (p - 1) * A_TILE + kk * 32);
                         const uint32_t acc = (first && kk == 0 && p == 1) ? 0u : 1u;
                         const int n0 = rows > 256 ? 256 : rows;
@@ -333,18 +343,23 @@ __global__ void k_emu_reduce(size_t n, int S, const double* __restrict__ W, doub
 
 namespace mot {
 
-int emu_prepare(mot_handle* h, const double* A, int M, int K, EmuMat* out) {
+int emu_prepare(mot_handle* h, const double* A, int M, int K, EmuMat* out, int nsl) {
     if (K % EK != 0) return fail(h, MOT_EINVAL, "emulated FP64 product: K must be a multiple of 32");
+    if (nsl != 4 && nsl != 6) return fail(h, MOT_EINVAL, "emulated product: 4 or 6 slices");
+    out->nsl = nsl;
     out->M = M;
     out->K = K;
     out->Mp = (M + EM - 1) / EM * EM;
     out->ea = (int*)dalloc(h, sizeof(int) * out->Mp);
-    out->a16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)NSL * out->Mp * K);
+    out->a16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)nsl * out->Mp * K);
     if (!out->ea || !out->a16) return fail(h, MOT_EOOM, "device allocation (emulated FP64 operator)");
     k_row_exponents<<<out->Mp, 256>>>(M, out->Mp, K, A, out->ea);
     const long long total = (long long)out->Mp * (K / 8);
-    k_slice_rows<<<(int)std::min<long long>((total + 255) / 256, 152 * 64), 256>>>(
-        M, out->Mp, K, A, out->ea, reinterpret_cast<__nv_bfloat16*>(out->a16));
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 64);
+    if (nsl == 6)
+        k_slice_rows<6><<<blocks, 256>>>(M, out->Mp, K, A, out->ea, reinterpret_cast<__nv_bfloat16*>(out->a16));
+    else
+        k_slice_rows<4><<<blocks, 256>>>(M, out->Mp, K, A, out->ea, reinterpret_cast<__nv_bfloat16*>(out->a16));
     h->launches += 2;
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "emulated FP64 operator set-up");
@@ -366,6 +381,7 @@ int launch_emu_gemm(mot_handle* h, const EmuMat& A, const double* X, int N, doub
     int S = std::max(1, std::min(nsm / std::max(1, MT * NH), (KT + KC_TILES - 1) / KC_TILES));
     int kts = ((KT + S - 1) / S + KC_TILES - 1) / KC_TILES * KC_TILES;
     S = (KT + kts - 1) / kts;
+    const int NSL = A.nsl;
     const size_t x16 = sizeof(uint16_t) * (size_t)NH * KT * NSL * EN * EK;
     const size_t part = S > 1 ? sizeof(double) * (size_t)S * A.M * N : 0;
     const size_t need = x16 + part + sizeof(int) * 256;
@@ -385,15 +401,25 @@ int launch_emu_gemm(mot_handle* h, const EmuMat& A, const double* X, int N, doub
     int* d_ex = reinterpret_cast<int*>(h->d_emuws + part + x16);
     k_col_exponents<<<N, 256, 0, s>>>(K, N, X, d_ex);
     const long long total = (long long)NH * EN * (K / 8);
-    k_slice_cols<<<(int)std::min<long long>((total + 255) / 256, 152 * 32), 256, 0, s>>>(K, N, NH, X, d_ex, d_x16);
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_emu_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)E_SMEM);
+        cudaFuncSetAttribute(k_emu_gemm<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EmuCfg<6>::SMEM);
+        cudaFuncSetAttribute(k_emu_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EmuCfg<4>::SMEM);
         attr = true;
     }
     dim3 grid(MT, NH, S);
-    k_emu_gemm<<<grid, E_THREADS, E_SMEM, s>>>(A.M, N, K, kts, reinterpret_cast<const __nv_bfloat16*>(A.a16), A.ea,
-                                               d_x16, d_ex, S > 1 ? ws : Y, h->d_cg_iters + 2);
+    const auto* a16 = reinterpret_cast<const __nv_bfloat16*>(A.a16);
+    double* out = S > 1 ? ws : Y;
+    if (NSL == 6) {
+        k_slice_cols<6><<<blocks, 256, 0, s>>>(K, N, NH, X, d_ex, d_x16);
+        k_emu_gemm<6><<<grid, E_THREADS, EmuCfg<6>::SMEM, s>>>(A.M, N, K, kts, a16, A.ea, d_x16, d_ex, out,
+                                                               h->d_cg_iters + 2);
+    } else {
+        k_slice_cols<4><<<blocks, 256, 0, s>>>(K, N, NH, X, d_ex, d_x16);
+        k_emu_gemm<4><<<grid, E_THREADS, EmuCfg<4>::SMEM, s>>>(A.M, N, K, kts, a16, A.ea, d_x16, d_ex, out,
+                                                               h->d_cg_iters + 2);
+    }
     h->launches += 3;
     if (S > 1) {
         const size_t n = (size_t)A.M * N;

@@ -266,6 +266,12 @@ void left_factor(mot_handle* h, const Work& W, const double* y1, const double* y
 
 bool mixed(const mot_handle* h) { return h->opt.precision == MOT_PREC_MIXED && h->d_Q0 && !h->precomputing; }
 bool mflag(const mot_handle* h, int bit) { return (h->opt.mixed_flags & bit) != 0; }
+// emulated products on the tensor cores: requested and an sm_100-family GPU
+bool emu_ok(const mot_handle* h) {
+    int major = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
+    return mflag(h, MOT_MIX_EMU64) && major == 10;
+}
 
 // out = Q_0 v with the dense FP64 Q_0 (the refinement residual of the mixed path)
 void apply_q0_dense64(mot_handle* h, const double* v, double* out, cudaStream_t s) {
@@ -282,13 +288,21 @@ void apply_q0(mot_handle* h, const Work& W, const double* v, double* out, cudaSt
     if (mixed(h)) {
         const double* in = v;
         if (h->prec_active) {  // right preconditioning: Q_0 (M v)
-            launch_d2f(h, bv, v, h->d_xf, s);
-            launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Minvf, h->d_xf, W.q1, s);
+            if (h->emu_Minv.a16) {
+                launch_emu_gemm(h, h->emu_Minv, v, h->B, W.q1, s);
+            } else {
+                launch_d2f(h, bv, v, h->d_xf, s);
+                launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Minvf, h->d_xf, W.q1, s);
+            }
             in = W.q1;
         }
         if (mflag(h, MOT_MIX_Q032)) {
-            launch_d2f(h, bv, in, h->d_xf, s);
-            launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Q0f, h->d_xf, out, s);
+            if (h->emu_Q0s.a16) {
+                launch_emu_gemm(h, h->emu_Q0s, in, h->B, out, s);
+            } else {
+                launch_d2f(h, bv, in, h->d_xf, s);
+                launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Q0f, h->d_xf, out, s);
+            }
         } else {
             apply_q0_dense64(h, in, out, s);
         }
@@ -372,8 +386,12 @@ int prec_solve(mot_handle* h, const Work& W, const double* rhs, double* x, doubl
     h->prec_active = true;
     int st = gmres(h, W, rhs, W.pd, false, tol, s);
     h->prec_active = false;
-    launch_d2f(h, (size_t)h->npad * 2 * h->B, W.pd, h->d_xf, s);
-    launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Minvf, h->d_xf, x, s);
+    if (h->emu_Minv.a16) {
+        launch_emu_gemm(h, h->emu_Minv, W.pd, h->B, x, s);
+    } else {
+        launch_d2f(h, (size_t)h->npad * 2 * h->B, W.pd, h->d_xf, s);
+        launch_sgemm_d(h, 2 * h->npad, h->B, 2 * h->npad, h->d_Minvf, h->d_xf, x, s);
+    }
     return st;
 }
 
@@ -1219,6 +1237,10 @@ int precompute_mixed(mot_handle* h) {
         }
         dense_inverse_from_lu(h, (int)n2, lu, piv, inv, s);
         launch_d2f(h, (size_t)n2 * n2, inv, h->d_Minvf, s);
+        if (emu_ok(h)) {  // 4-slice copy for the tensor-core products of the FP32 solves
+            CK(cudaDeviceSynchronize());
+            if ((st = emu_prepare(h, inv, (int)n2, (int)n2, &h->emu_Minv, 4)) != MOT_OK) return st;
+        }
         CK(cudaDeviceSynchronize());
         cudaFree(lu);
         cudaFree(inv);
@@ -1258,11 +1280,12 @@ int precompute_mixed(mot_handle* h) {
     free_state(h);
     h->precomputing = false;
     if (it[1] > 0) return fail(h, MOT_ENOCONV, "a CG solve did not converge while assembling the dense operators");
-    int major = 0;
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
-    if (mflag(h, MOT_MIX_EMU64) && major == 10) {  // slices of Q_0 and [M1 | M2] for the emulated FP64 products
-        if ((st = emu_prepare(h, h->d_Q0, 2 * h->npad, 2 * h->npad, &h->emu_Q0)) != MOT_OK) return st;
-        if ((st = emu_prepare(h, h->d_LF, h->npad, 2 * h->npad, &h->emu_LF)) != MOT_OK) return st;
+    if (emu_ok(h)) {  // slices of Q_0 and [M1 | M2] for the emulated products
+        if ((st = emu_prepare(h, h->d_Q0, 2 * h->npad, 2 * h->npad, &h->emu_Q0, 6)) != MOT_OK) return st;
+        if ((st = emu_prepare(h, h->d_LF, h->npad, 2 * h->npad, &h->emu_LF, 6)) != MOT_OK) return st;
+        if (mflag(h, MOT_MIX_Q032) &&
+            (st = emu_prepare(h, h->d_Q0, 2 * h->npad, 2 * h->npad, &h->emu_Q0s, 4)) != MOT_OK)
+            return st;
         CK(cudaDeviceSynchronize());
     }
     if (h32) {  // the FP64 history tiles are no longer read
@@ -1584,6 +1607,8 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16, h->d_sgws, h->d_emuws};
     emu_free(h, &h->emu_Q0);
     emu_free(h, &h->emu_LF);
+    emu_free(h, &h->emu_Q0s);
+    emu_free(h, &h->emu_Minv);
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);

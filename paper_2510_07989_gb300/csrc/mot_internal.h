@@ -40,7 +40,7 @@ struct HistChunk {
 // six bf16 integer slices per value (rows scaled by 2^-ea), pre-arranged in
 // the MMA's layout, [Mp / 128][K / 32][6][128 x 32].
 struct EmuMat {
-    int M = 0, K = 0, Mp = 0;
+    int M = 0, K = 0, Mp = 0, nsl = 6;  // slices per value: 6 (FP64-accurate) or 4 (beyond FP32)
     int* ea = nullptr;        // [Mp] row exponents
     uint16_t* a16 = nullptr;  // slices
 };
@@ -169,6 +169,7 @@ struct mot_handle {
     double* d_sgws = nullptr;      // split-K partial results of the FP32 dense products
     size_t sgws_bytes = 0;
     EmuMat emu_Q0, emu_LF;         // Q_0 and [M1 | M2] for the emulated FP64 products (MOT_MIX_EMU64)
+    EmuMat emu_Q0s, emu_Minv;      // Q_0 and Q_0^{-1} with 4 slices: the products of the FP32 solves
     unsigned char* d_emuws = nullptr;  // their per-call workspace (X slices, split-K partials)
     size_t emuws_bytes = 0;
     float* d_Minvf = nullptr;      // FP32 Q_0^{-1} (GMRES preconditioner), (2 npad)^2
@@ -219,7 +220,7 @@ bool history_tc_fits(int npad);  // the row block's column order fits in shared 
 
 // emulated FP64 products on tensor cores (k_emu64.cu): Y (M x N) = A X with A
 // prepared once by emu_prepare from the device FP64 matrix A (M x K, ld K)
-int emu_prepare(mot_handle* h, const double* A, int M, int K, EmuMat* out);
+int emu_prepare(mot_handle* h, const double* A, int M, int K, EmuMat* out, int nsl);
 void emu_free(mot_handle* h, EmuMat* m);
 int launch_emu_gemm(mot_handle* h, const EmuMat& A, const double* X, int N, double* Y, cudaStream_t s);
 
