@@ -155,9 +155,7 @@ class Clocks:
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:k_hist_tc -s 56 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline
-    ("k_hist_tc", "torus64x24"): (47749068800 + 230510848, "4f02357985304f7f63f8fa1f4718af96ba79c41f"),
-    # the same on --workload torus32x12
-    ("k_hist_tc", "torus32x12"): (4477955328 + 17707008, "4f02357985304f7f63f8fa1f4718af96ba79c41f"),
+    ("k_hist_tc", "torus64x24"): (47713468672 + 230661632, "9934e9e9d71ab761fe11287efe7153efd4377024"),
 }
 
 

@@ -364,6 +364,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- gather: coefficient rows and the tile copy ----------------
         const int t = tid;
         const int l8 = lane & 7, l3 = lane >> 3;
+        const int slot_i = (int)(step_i % R);  // ring slot of step i; lag k (< R) is slot_i - k mod R
         // this lane's 16-byte pieces: slices q = 0..2, row groups ro, column quads mq of
         // its warp's half (mq = 2 warp + 0/1); destination offsets do not depend on the task
         uint32_t dofs[4][2];
@@ -396,7 +397,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             const int part = code & 3, var = (code >> 2) & 3;
             const __nv_bfloat16* pan = part == 2 ? win16 + (size_t)k * 3 * pstride
-                                                 : ring16 + (((size_t)((step_i - k) % R) * 2 + part) * 3) * pstride;
+                                                 : ring16 + (((size_t)(slot_i - k + (slot_i < k ? R : 0)) * 2 + part) * 3) * pstride;
             const int swap = (part != 2 && var == 2) ? 8 : 0;  // [-v, u]: 64-column halves exchanged
             const uint32_t adst = sbase + s * STAGE;
 #pragma unroll
