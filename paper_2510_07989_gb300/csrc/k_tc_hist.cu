@@ -18,15 +18,15 @@
 // of two bf16 values are exact in the FP32 accumulator). With Y, Z the tiles
 // of s1 and s2, the six tile slices are stacked along N as [Y0 Z0 Y1 Z1 Y2 Z2]
 // (32 rows each), so per K-half the tensor core runs
-//   P0 x [Y0 Z0 Y1 Z1] (N = 128) into TMEM columns [0, 128),
-//   P0 x [Y2 Z2], P1 x [Y0 Z0], P1 x [Y1 Z1], P2 x [Y0 Z0] (N = 64 each)
-//   into columns [64, 128):
+//   P0 x [Y0 Z0 Y1 Z1 Y2 Z2] (N = 192) into TMEM columns [0, 192),
+//   P1 x [Y0 Z0 Y1 Z1]       (N = 128) into columns [64, 192),
+//   P2 x [Y0 Z0]             (N = 64)  into columns [128, 192):
 // columns [0, 64) hold only P0 Y0 | P0 Z0, [64, 128) the terms of relative
-// size 2^-8 and 2^-16 (their FP32 rounding is 2^-8 below that of the leading
-// block); per output the two blocks sum to P Y - (P1 Y2 + P2 Y1 + P2 Y2), a
-// relative truncation of about 2^-26. With 128 columns per buffer, four
-// buffers fit in TMEM, so the MMA issue runs up to four groups ahead of the
-// epilogue.
+// size 2^-8, [128, 192) those of size 2^-16; per output the three blocks sum
+// to P Y - (P1 Y2 + P2 Y1 + P2 Y2), a relative truncation of about 2^-26.
+// Three MMAs per K-half, six per task: fewer, wider MMAs than one per
+// (slice, slice) pair, since every instruction costs the single issuing
+// thread the same whatever its N.
 // The tensor core's FP32 accumulation rounds once per MMA at the scale of the
 // accumulator, so the large block sees only two additions per task; after
 // FGROUP tasks the epilogue warps fold the buffer into a compensated FP32 pair
@@ -69,8 +69,8 @@ namespace {
 
 constexpr int T = MOT_TILE;                 // 32
 constexpr int TC_M = 128;                   // 2B columns per coefficient panel
-constexpr int NB = 4;                       // TMEM accumulator buffers
-constexpr int BUFCOLS = 128;                // TMEM columns per buffer (two magnitudes x two outputs x 32)
+constexpr int NB = 2;                       // TMEM accumulator buffers
+constexpr int BUFCOLS = 192;                // TMEM columns per buffer (three magnitudes x two outputs x 32)
 constexpr int TMEM_COLS = 512;              // allocation (power of two >= NB * BUFCOLS)
 constexpr int FGROUP = 2;                   // tasks per TMEM accumulation
 constexpr int A_SLICE = TC_M * T * 2;       // 8192 bytes: one bf16 slice of a 128 x 32 panel
@@ -447,14 +447,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // B columns 16 kk .. (32 bytes into each 64-byte row)
 #pragma unroll
                 for (int kk = 0; kk < 2; kk++) {
-                    const uint64_t p0 = desc_a_sw128(a0 + kk * 2048), p1 = desc_a_sw128(a0 + A_SLICE + kk * 2048),
-                                   p2 = desc_a_sw128(a0 + 2 * A_SLICE + kk * 2048);
-                    // B rows: Y0 Z0 at 0, Y1 Z1 at 64 (4 KB), Y2 Z2 at 128 (8 KB)
-                    mma_bf16(dcol, p0, desc_b_sw64(b0 + kk * 32), idesc_bf16(128), (ing > 0 || kk > 0) ? 1u : 0u);
-                    mma_bf16(dcol + 64, p0, desc_b_sw64(b0 + 8192 + kk * 32), idesc_bf16(64), 1u);
-                    mma_bf16(dcol + 64, p1, desc_b_sw64(b0 + kk * 32), idesc_bf16(64), 1u);
-                    mma_bf16(dcol + 64, p1, desc_b_sw64(b0 + 4096 + kk * 32), idesc_bf16(64), 1u);
-                    mma_bf16(dcol + 64, p2, desc_b_sw64(b0 + kk * 32), idesc_bf16(64), 1u);
+                    const uint64_t bd = desc_b_sw64(b0 + kk * 32);
+                    mma_bf16(dcol, desc_a_sw128(a0 + kk * 2048), bd, idesc_bf16(192), (ing > 0 || kk > 0) ? 1u : 0u);
+                    mma_bf16(dcol + 64, desc_a_sw128(a0 + A_SLICE + kk * 2048), bd, idesc_bf16(128), 1u);
+                    mma_bf16(dcol + 128, desc_a_sw128(a0 + 2 * A_SLICE + kk * 2048), bd, idesc_bf16(64), 1u);
                 }
                 tc_commit(EMPTY(s));
                 ing++;
@@ -482,11 +478,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     xs2 = ucol ? -1.f : 1.f;
         // folds buffer b (transform key) into the sums of output o
         auto fold = [&](uint32_t col, float c, float (&hs)[32], float (&hc)[32], bool release, int b) {
-            float va[32];
-            tmem_ld32(col + 64, va);  // terms of relative size 2^-8 and 2^-16
+            float va[32], vb[32];
+            tmem_ld32(col + 64, va);   // terms of relative size 2^-8
+            tmem_ld32(col + 128, vb);  // and 2^-16
             tmem_wait_ld();
 #pragma unroll
-            for (int n = 0; n < 32; n++) hc[n] += c * va[n];
+            for (int n = 0; n < 32; n++) hc[n] += c * (va[n] + vb[n]);
             tmem_ld32(col, va);  // the leading products
             tmem_wait_ld();
             if (release) {
