@@ -104,8 +104,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+// Raise the barrier's expected transaction count without arriving.
+__device__ __forceinline__ void mbar_add_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
@@ -298,12 +299,14 @@ __device__ __forceinline__ int task_xform(int code) { return (code & 3) == 2 ? 3
 
 template <int NS>
 struct TcLayout {
-    static constexpr int NBARS = 3 * NS + 2 * NB + 1;  // + one barrier for the final MMA drain
+    static constexpr int NBARS = 2 * NS + 2 * NB + 1;  // + one barrier for the final MMA drain
     static constexpr size_t BARS = (size_t)NS * STAGE;
-    static constexpr size_t SLOT = BARS + 8 * NBARS;        // TMEM address, abort flag
-    static constexpr size_t DESC = SLOT + 16;               // TC_CHUNK packed tasks
-    static constexpr size_t COLS = DESC + 16 * TC_CHUNK;    // column order of the row block (uint16)
+    static constexpr size_t SLOT = BARS + ((8 * NBARS + 15) / 16) * 16;  // TMEM address, abort flag
+    static constexpr size_t DESC = SLOT + 16;                             // TC_CHUNK packed tasks (uint4)
+    static constexpr size_t COLS = DESC + 16 * TC_CHUNK;                  // column order of the row block (uint16)
     static size_t bytes(int npad) { return COLS + (((size_t)npad * 2 + 15) / 16) * 16 + 1024; }
+    static_assert(BARS % 1024 == 0 && SLOT % 16 == 0 && DESC % 16 == 0 && COLS % 16 == 0,
+                  "shared-memory regions must keep their alignment (uint4 task loads)");
 };
 
 template <int NS>
@@ -323,12 +326,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     uint4* sdesc = reinterpret_cast<uint4*>(smem + L::DESC);
     uint16_t* scol = reinterpret_cast<uint16_t*>(smem + L::COLS);
-    auto FULL_A = [&](int s) { return bar0 + 8u * s; };            // coefficient rows landed
-    auto TFULL = [&](int s) { return bar0 + 8u * (NS + s); };      // tile slices landed
-    auto EMPTY = [&](int s) { return bar0 + 8u * (2 * NS + s); };  // MMAs done with the stage
-    auto ACCF = [&](int b) { return bar0 + 8u * (3 * NS + b); };
-    auto ACCE = [&](int b) { return bar0 + 8u * (3 * NS + NB + b); };
-    const uint32_t DRAIN = bar0 + 8u * (3 * NS + 2 * NB);
+    // FULL: the coefficient rows (one arrival per copying thread, when its
+    // cp.async copies have landed) and the tile slices (bytes of the bulk
+    // copies, added to the barrier's transaction count) of a stage
+    auto FULL = [&](int s) { return bar0 + 8u * s; };
+    auto EMPTY = [&](int s) { return bar0 + 8u * (NS + s); };  // MMAs done with the stage
+    auto ACCF = [&](int b) { return bar0 + 8u * (2 * NS + b); };
+    auto ACCE = [&](int b) { return bar0 + 8u * (2 * NS + NB + b); };
+    const uint32_t DRAIN = bar0 + 8u * (2 * NS + 2 * NB);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const HistChunk ch = chunks[blockIdx.x];
@@ -339,8 +344,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int p = tid; p < npad; p += TC_THREADS) scol[p] = (uint16_t)colidx[(size_t)ch.rb * npad + p];
     if (tid == 0) {
         for (int s = 0; s < NS; s++) {
-            mbar_init(FULL_A(s), NPROD);
-            mbar_init(TFULL(s), 1);
+            mbar_init(FULL(s), NPROD);
             mbar_init(EMPTY(s), 1);
         }
         for (int b = 0; b < NB; b++) {
@@ -385,14 +389,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ok = false;
                 break;
             }
-            if (t == 0) {  // slices in the order Y0 Z0 Y1 Z1 Y2 Z2
-                mbar_expect_tx(TFULL(s), STAGE_B);
+            if (t == 0) {  // slices in the order Y0 Z0 Y1 Z1 Y2 Z2; bytes added before this thread's arrival
+                mbar_add_tx(FULL(s), STAGE_B);
 #pragma unroll
                 for (int q = 0; q < 3; q++) {
                     bulk_g2s(sbase + s * STAGE + STAGE_A + (2 * q) * B_SLICE, tiles16 + ((size_t)d.x * 3 + q) * (T * T),
-                             B_SLICE, TFULL(s));
+                             B_SLICE, FULL(s));
                     bulk_g2s(sbase + s * STAGE + STAGE_A + (2 * q + 1) * B_SLICE,
-                             tiles16 + ((size_t)d.y * 3 + q) * (T * T), B_SLICE, TFULL(s));
+                             tiles16 + ((size_t)d.y * 3 + q) * (T * T), B_SLICE, FULL(s));
                 }
             }
             const int part = code & 3, var = (code >> 2) & 3;
@@ -410,14 +414,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int q = 0; q < 3; q++) cp_async16(adst + q * A_SLICE + dofs[ro][h], src + (size_t)q * pstride);
                 }
             }
-            // the stage's FULL_A arrival fires when these copies have landed
-            cp_async_arrive_noinc(FULL_A(s));
+            // this thread's arrival on the stage fires when its copies have landed
+            cp_async_arrive_noinc(FULL(s));
             issued = j + 1;
         }
         cp_async_wait_all();
         if (!ok && t == 0)  // let the tile copies in flight land before the CTA exits
             for (int jj = issued > NS ? issued - NS : 0; jj < issued; jj++)
-                mbar_wait_drain(TFULL(jj % NS), (uint32_t)(jj / NS) & 1u);
+                mbar_wait_drain(FULL(jj % NS), (uint32_t)(jj / NS) & 1u);
     } else if (warp == 2) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -438,8 +442,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     dcol = tmem + (uint32_t)(b * BUFCOLS);
                 }
                 const int s = j % NS;
-                if (!mbar_wait(FULL_A(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 4)) break;
-                if (!mbar_wait(TFULL(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 6)) break;
+                if (!mbar_wait(FULL(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 4)) break;
                 fence_proxy_async();  // coefficient rows written by cp.async (generic proxy)
                 tc_fence_after();
                 const uint32_t a0 = sbase + s * STAGE, b0 = a0 + STAGE_A;
