@@ -155,7 +155,7 @@ class Clocks:
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:k_hist_tc -s 56 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline
-    ("k_hist_tc", "torus64x24"): (47713468672 + 230661632, "9934e9e9d71ab761fe11287efe7153efd4377024"),
+    ("k_hist_tc", "torus64x24"): (47718425000 + 231234304, "2076df85d836f272042a68874fb11aee75cd28ad"),
 }
 
 
