@@ -223,6 +223,30 @@ int mot_step(mot_handle* h, const mot_wave* waves, int B, double* w_out, void* s
 /* n_steps calls of mot_step; w_out (nullable) receives [n_steps][B][2][ne]. */
 int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, double* w_out, void* stream);
 
+/*
+ * March n scatterers of uneven sizes n_steps each, concurrently (the batched
+ * uneven-scatterer run). Scatterer i is marched as by
+ *   mot_run(hs[i], n_steps, waves[i], B[i], w_out ? w_out[i] : NULL, .)
+ * on a stream of its own driven by a host thread of its own: each stream
+ * starts after the work already queued on `stream` and `stream` waits for all
+ * of them before its later work, so the latency-bound solves of the small
+ * scatterers overlap the kernels of the large ones. Each scatterer's results
+ * are those of the single mot_run (the same kernels in the same order).
+ *   hs      : n distinct handles with operators loaded, on the device of
+ *             `stream` (a cudaStream_t, or NULL for the default stream).
+ *   waves   : n arrays, waves[i] holding B[i] plane waves (host).
+ *   B       : n batch sizes, each in [1, 64] (fixed per handle as in mot_step).
+ *   w_out   : NULL, or n pointers, each NULL or [n_steps][B[i]][2][ne_i]
+ *             doubles in host or device memory.
+ * Returns MOT_OK; MOT_ENOCONV if a step of some scatterer hit an iteration
+ * limit; otherwise the error of the lowest-indexed scatterer that failed (its
+ * message in that handle's mot_last_error; the others still finish). Errors
+ * found before any work: MOT_EINVAL (n < 0, n_steps < 0, a NULL or repeated
+ * handle, NULL waves or B). n == 0 returns MOT_OK.
+ */
+int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* const* waves, const int* B,
+                 double* const* w_out, void* stream);
+
 /* Recovered currents of the last step, [B][4][ne]: j loop, j star, m loop,
  * m star (Eq. (dis_jm)), host or device memory. */
 int mot_get_currents(mot_handle* h, double* out);

@@ -402,12 +402,11 @@ int launch_emu_gemm(mot_handle* h, const EmuMat& A, const double* X, int N, doub
     k_col_exponents<<<N, 256, 0, s>>>(K, N, X, d_ex);
     const long long total = (long long)NH * EN * (K / 8);
     const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    once_per_device(attr, h->dev, [] {
         cudaFuncSetAttribute(k_emu_gemm<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EmuCfg<6>::SMEM);
         cudaFuncSetAttribute(k_emu_gemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EmuCfg<4>::SMEM);
-        attr = true;
-    }
+    });
     dim3 grid(MT, NH, S);
     const auto* a16 = reinterpret_cast<const __nv_bfloat16*>(A.a16);
     double* out = S > 1 ? ws : Y;

@@ -416,11 +416,10 @@ void launch_history32(mot_handle* h, const TaskList& tl, const float* tiles, con
         if (timed) cudaEventRecord(h->ev0, s);
         if (C2 == V2_C && mode == 0) {
             const size_t smem = sizeof(double) * 2 * T * V2_C + sizeof(float) * 2 * T * (V2_AS + V2_BS);
-            static bool attr = false;
-            if (!attr) {
+            static std::atomic<unsigned long long> attr{0};
+            once_per_device(attr, h->dev, [smem] {
                 cudaFuncSetAttribute(k_hist_f32_b128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                attr = true;
-            }
+            });
             k_hist_f32_b128<<<tl.nchunks, 128, smem, s>>>(tl.tasks, tl.chunks, tiles, ring, win, step_i, h->R,
                                                           h->npad, h->d_colidx, h->d_partial);
         } else {

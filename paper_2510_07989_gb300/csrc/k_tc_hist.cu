@@ -672,13 +672,12 @@ void launch_history_tc(mot_handle* h, const TaskList& tl, long long step_i, doub
     if (tl.nchunks > 0) {
         const bool timed = h->opt.timing && h->ev0 && step_i > h->K;
         if (timed) cudaEventRecord(h->ev0, s);
-        static bool attr = false;
-        if (!attr) {
+        static std::atomic<unsigned long long> attr{0};
+        once_per_device(attr, h->dev, [] {
             cudaFuncSetAttribute(k_hist_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
             cudaFuncSetAttribute(k_hist_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
             cudaFuncSetAttribute(k_hist_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-            attr = true;
-        }
+        });
         const uint4* pt = tl.packed;
         const auto* r16 = reinterpret_cast<const __nv_bfloat16*>(h->d_ring16);
         const auto* w16 = reinterpret_cast<const __nv_bfloat16*>(h->d_win16);

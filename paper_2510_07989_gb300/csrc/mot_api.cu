@@ -45,7 +45,14 @@ void* dalloc(mot_handle* h, size_t bytes) {
         cudaGetLastError();
         return nullptr;
     }
-    cudaMemset(p, 0, bytes);
+    // Zeroed before returning: the memory may next be used from a non-blocking
+    // stream (mot_run_many), which is not ordered after the legacy stream that
+    // cudaMemset runs on, and cudaMemset may return before it has run.
+    if (cudaMemset(p, 0, bytes) != cudaSuccess || cudaStreamSynchronize(nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(p);
+        return nullptr;
+    }
     h->device_bytes += (int64_t)bytes;
     return p;
 }
@@ -422,8 +429,6 @@ int ensure_state(mot_handle* h, int B) {
             h->d_ring16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)h->R * 6 * bv);
             h->d_win16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)(h->max_tail_lag + 1) * 3 * bv);
             if (!h->d_ring16 || !h->d_win16) return fail(h, MOT_EOOM, "device allocation of the march state");
-            CK(cudaMemset(h->d_ring16, 0, sizeof(uint16_t) * (size_t)h->R * 6 * bv));
-            CK(cudaMemset(h->d_win16, 0, sizeof(uint16_t) * (size_t)(h->max_tail_lag + 1) * 3 * bv));
         } else {
             h->d_ring32 = (float*)dalloc(h, sizeof(float) * (size_t)h->R * 6 * bv);
             h->d_win32 = (float*)dalloc(h, sizeof(float) * (size_t)(h->max_tail_lag + 1) * bv);
@@ -1415,6 +1420,73 @@ MOT_API int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, do
         int st = mot_step(h, waves, B, dst, stream);
         if (st == MOT_ENOCONV) worst = st;
         else if (st != MOT_OK) return st;
+    }
+    return worst;
+}
+
+MOT_API int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* const* waves, const int* B,
+                         double* const* w_out, void* stream) {
+    if (n < 0 || n_steps < 0) return MOT_EINVAL;
+    if (n == 0) return MOT_OK;
+    if (!hs || !waves || !B) return MOT_EINVAL;
+    {
+        std::vector<const mot_handle*> seen(hs, hs + n);
+        std::sort(seen.begin(), seen.end());
+        if (std::adjacent_find(seen.begin(), seen.end()) != seen.end()) return MOT_EINVAL;
+        for (int i = 0; i < n; i++)
+            if (!hs[i] || !waves[i]) return MOT_EINVAL;
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    std::vector<int> st(n, MOT_OK);
+    // fork: every scatterer's stream waits for the work queued on `stream`
+    cudaEvent_t fork = nullptr;
+    {
+        mot_handle* h0 = hs[0];
+        cudaError_t e = cudaSetDevice(h0->dev);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, user);
+        if (e != cudaSuccess) {
+            if (fork) cudaEventDestroy(fork);
+            return cuda_fail(h0, e, "mot_run_many: fork event");
+        }
+    }
+    std::vector<cudaEvent_t> joins(n, nullptr);
+    auto march = [&](int i) {
+        mot_handle* h = hs[i];
+        if (cudaSetDevice(h->dev) != cudaSuccess) {
+            st[i] = fail(h, MOT_ECUDA, "cudaSetDevice");
+            return;
+        }
+        cudaStream_t s = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork, 0);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            st[i] = cuda_fail(h, e, "mot_run_many: stream set-up");
+        } else {
+            st[i] = mot_run(h, n_steps, waves[i], B[i], w_out ? w_out[i] : nullptr, s);
+            e = cudaEventRecord(joins[i], s);  // the join point, recorded whatever the status
+            if (e != cudaSuccess && st[i] == MOT_OK) st[i] = cuda_fail(h, e, "mot_run_many: join event");
+        }
+        if (s) cudaStreamDestroy(s);  // released once its work completes
+    };
+    std::vector<std::thread> th;
+    th.reserve(n > 0 ? n - 1 : 0);
+    for (int i = 1; i < n; i++) th.emplace_back(march, i);
+    march(0);
+    for (auto& t : th) t.join();
+    // join: later work on `stream` waits for every scatterer
+    cudaSetDevice(hs[0]->dev);
+    for (int i = 0; i < n; i++)
+        if (joins[i]) {
+            cudaStreamWaitEvent(user, joins[i], 0);
+            cudaEventDestroy(joins[i]);
+        }
+    cudaEventDestroy(fork);
+    int worst = MOT_OK;
+    for (int i = 0; i < n; i++) {
+        if (st[i] != MOT_OK && st[i] != MOT_ENOCONV) return st[i];
+        if (st[i] == MOT_ENOCONV) worst = MOT_ENOCONV;
     }
     return worst;
 }

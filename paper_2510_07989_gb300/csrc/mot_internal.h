@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include <string>
 #include <vector>
 
@@ -197,6 +199,17 @@ namespace mot {
 
 // error helpers
 int fail(mot_handle* h, int code, const std::string& msg);
+
+// Runs f (an idempotent per-device setting, e.g. a kernel's shared-memory
+// attribute) the first time a call site reaches it on device dev; safe when
+// several host threads reach it at once (f may then run more than once).
+template <class F>
+inline void once_per_device(std::atomic<unsigned long long>& done, int dev, F&& f) {
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    f();
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
 int cuda_fail(mot_handle* h, cudaError_t e, const char* where);
 void* dalloc(mot_handle* h, size_t bytes);
 

@@ -73,7 +73,8 @@ class mot_info(ctypes.Structure):
         return d
 
 
-EXPORTED = ["mot_create", "mot_load_operators", "mot_set_frequencies", "mot_step", "mot_run", "mot_get_currents",
+EXPORTED = ["mot_create", "mot_load_operators", "mot_set_frequencies", "mot_step", "mot_run", "mot_run_many",
+            "mot_get_currents",
             "mot_fields", "mot_fields_noalloc", "mot_reset", "mot_save_state", "mot_load_state", "mot_get_info",
             "mot_get_edges", "mot_last_error", "mot_destroy"]
 
@@ -96,6 +97,7 @@ def load_library(path: str = LIB_PATH):
     lib.mot_set_frequencies.argtypes = [vp, i32, vp]
     lib.mot_step.argtypes = [vp, vp, i32, vp, vp]
     lib.mot_run.argtypes = [vp, i32, vp, i32, vp, vp]
+    lib.mot_run_many.argtypes = [vp, i32, i32, vp, vp, vp, vp]
     lib.mot_get_currents.argtypes = [vp, vp]
     lib.mot_fields.argtypes = [vp, vp, i32, vp, vp]
     lib.mot_fields_noalloc.argtypes = [vp, vp, i32, vp, vp]
@@ -237,6 +239,29 @@ def mot_step(h: Handle, waves, B: int, w_out=None, stream=None) -> int:
 def mot_run(h: Handle, n_steps: int, waves, B: int, w_out=None, stream=None) -> int:
     return _check(h.ptr, load_library().mot_run(h.ptr, int(n_steps), ctypes.cast(waves, ctypes.c_void_p), int(B),
                                                 _ptr(w_out), _stream(stream)), allow_noconv=True)
+
+
+def mot_run_many(handles, n_steps: int, waves_list, B_list, w_out_list=None, stream=None) -> int:
+    """mot_run_many: march len(handles) scatterers n_steps each, concurrently.
+    waves_list[i] is a mot_wave array of B_list[i] waves; w_out_list (None, or
+    one array or None per handle, [n_steps][B][2][ne] float64, numpy or torch
+    CUDA) receives the steps. Returns MOT_OK or MOT_ENOCONV; raises on other
+    errors with the messages of the handles that report one."""
+    n = len(handles)
+    lib = load_library()
+    hs = (ctypes.c_void_p * max(n, 1))(*[h.ptr for h in handles])
+    wv = (ctypes.c_void_p * max(n, 1))(*[ctypes.cast(w, ctypes.c_void_p).value for w in waves_list])
+    bs = (ctypes.c_int * max(n, 1))(*[int(b) for b in B_list])
+    outs = None
+    if w_out_list is not None:
+        outs = (ctypes.c_void_p * max(n, 1))(*[_ptr(o) for o in w_out_list])
+    code = lib.mot_run_many(hs if n else None, n, int(n_steps), wv if n else None, bs if n else None, outs,
+                            _stream(stream))
+    if code in (MOT_OK, MOT_ENOCONV):
+        return code
+    msgs = [f"[{i}] {lib.mot_last_error(h.ptr).decode()}" for i, h in enumerate(handles)
+            if lib.mot_last_error(h.ptr)]
+    raise MotError(code, "; ".join(msgs))
 
 
 def mot_get_currents(h: Handle, out) -> None:

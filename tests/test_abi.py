@@ -55,3 +55,25 @@ def test_create_rejects_bad_input(lib):
     with pytest.raises(M.MotError) as e:
         M.mot_create(m.verts, bad, 2.0, 1.0, 0.2, 40)          # inconsistent orientation
     assert e.value.code == M.MOT_EINVAL
+
+
+def test_run_many_rejects_bad_input_before_any_work(lib):
+    """mot_run_many validates its arguments before touching a handle or the GPU."""
+    import ctypes
+    from paper_2510_07989_gb300 import mot as M
+    assert lib.mot_run_many(None, -1, 1, None, None, None, None) == M.MOT_EINVAL
+    assert lib.mot_run_many(None, 1, -1, None, None, None, None) == M.MOT_EINVAL
+    assert lib.mot_run_many(None, 0, 5, None, None, None, None) == M.MOT_OK  # nothing to march
+    assert lib.mot_run_many(None, 1, 5, None, None, None, None) == M.MOT_EINVAL
+    # a repeated handle is refused (checked by address only, never dereferenced)
+    fake = ctypes.create_string_buffer(64)
+    hs = (ctypes.c_void_p * 2)(ctypes.addressof(fake), ctypes.addressof(fake))
+    wv = (ctypes.c_void_p * 2)(ctypes.addressof(fake), ctypes.addressof(fake))
+    bs = (ctypes.c_int * 2)(1, 1)
+    assert lib.mot_run_many(hs, 2, 5, wv, bs, None, None) == M.MOT_EINVAL
+    # a NULL handle or wave array among them is refused too
+    hs2 = (ctypes.c_void_p * 2)(ctypes.addressof(fake), None)
+    assert lib.mot_run_many(hs2, 2, 5, wv, bs, None, None) == M.MOT_EINVAL
+    wv2 = (ctypes.c_void_p * 2)(None, ctypes.addressof(fake))
+    hs3 = (ctypes.c_void_p * 2)(ctypes.addressof(fake), ctypes.addressof(fake) + 8)
+    assert lib.mot_run_many(hs3, 2, 5, wv2, bs, None, None) == M.MOT_EINVAL
