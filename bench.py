@@ -20,6 +20,7 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import math
 import os
@@ -49,7 +50,7 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="torus64x24", choices=sorted(WORKLOADS))
@@ -97,10 +98,42 @@ def make_workload(name, rank=0):
     return ops, exc, t_asm
 
 
-class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+
+def parse_clock_csv(lines, t_begin=None, t_end=None, slack=0.25):
+    """Clock record of a region from nvidia-smi CSV lines (timestamp, index,
+    clocks.sm, clocks.max.sm, power.draw, clocks_event_reasons.active and the
+    four reasons of CLOCK_REASONS): median SM clock and the active reasons of
+    the samples taken within [t_begin - slack, t_end + slack] (host epoch
+    seconds; no window: every sample)."""
+    sm, smax, reasons, n_all = [], [], set(), 0
+    for line in lines:
+        p = [x.strip() for x in line.split(",")]
+        if len(p) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            f_sm, f_max = float(p[2]), float(p[3])
+        except ValueError:
+            continue
+        n_all += 1
+        if t_begin is not None and not (t_begin - slack <= ts <= t_end + slack):
+            continue
+        sm.append(f_sm)
+        smax.append(f_max)
+        for nm, v in zip(CLOCK_REASONS, p[6:10]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+            "samples": len(sm), "samples_outside_region": n_all - len(sm), "reasons": sorted(reasons)}
+
+
+class Clocks:
+    """nvidia-smi sampling (every 200 ms) of SM clocks and throttle reasons;
+    the record keeps the samples taken between begin() and end()."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -108,8 +141,10 @@ class Clocks:
         self.dev = device_index
         self.proc = None
         self.path = None
+        self.t_begin = self.t_end = None
 
     def start(self):
+        """Start the sampler and wait (up to 5 s) for its first sample."""
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -119,6 +154,16 @@ class Clocks:
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t = time.time()
+        while time.time() - t < 5.0 and self.proc.poll() is None and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
+
+    def begin(self):
+        self.t_begin = time.time()
+
+    def end(self):
+        self.t_end = time.time()
 
     def stop(self):
         if self.proc is None:
@@ -129,23 +174,12 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                sm.append(float(p[1]))
-                smax.append(float(p[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, p[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
+        with open(self.path) as f:
+            rec = parse_clock_csv(f.readlines(), self.t_begin, self.t_end)
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        if self.t_begin is not None:
+            rec["region_s"] = round(self.t_end - self.t_begin, 3)
+        return rec
 
 
 # DRAM bytes (read + write) of one full-depth history launch, from one ncu
@@ -233,30 +267,32 @@ def run_reference(args):
     ne = ops.ne
     K = ops.kmax + 1
     rng = np.random.default_rng(7)
-    total = args.warmup + args.steps + K + 8
-    L = np.zeros((total + 2, 2 * ne))
-    S = np.zeros((total + 2, 2 * ne))
+    L = np.zeros((K + 4, 2 * ne))
+    S = np.zeros((K + 4, 2 * ne))
     for j in range(1, K + 2):
         L[j], S[j] = sysP.split(rng.standard_normal(2 * ne) * 1e-3)
     i = K + 2
-    for _ in range(args.warmup):
-        w = sysP.step(exc, 0, i, L, S)
-        L[i], S[i] = sysP.split(w)
-        i += 1
+    # The K bench steps of this arm are together ONE full-depth product-form
+    # MOT step for one right-hand side (each bench step 1/K of it): an oracle
+    # step takes about a minute on the host cores, so K whole steps would not
+    # end within minutes. Warm-up: one Q_0 application (the code paths of the
+    # step's solve).
+    if args.warmup > 0:
+        sysP.q0(L[K + 1] + S[K + 1])
     t0 = time.time()
-    for _ in range(args.steps):
-        w = sysP.step(exc, 0, i, L, S)
-        L[i], S[i] = sysP.split(w)
-        i += 1
+    w = sysP.step(exc, 0, i, L, S)
     el = time.time() - t0
-    v = args.steps / el
+    assert np.all(np.isfinite(w))
+    v = 1.0 / el  # one RHS-step
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "RHS·steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "rhs_per_step": 1},
             "cpu_baseline": {"value": v, "unit": "RHS·steps/s", "cores": cores, "kind": "oracle",
-                             "sample": "each step: one full-depth MOT step x 1 RHS (product-form FP64 oracle)"},
+                             "sample": "one full-depth MOT step x 1 RHS of the same workload (product-form FP64 "
+                                       "oracle, seeded history), timed as the K bench steps (each 1/K of it); "
+                                       "warm-up: one Q_0 application; setup excluded"},
             "e2e": {"value": v, "unit": "RHS·steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -285,6 +321,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     K = ops.kmax + 1
     # fill the history to full depth, then the requested warm-up
+    clocks = Clocks(local)
+    clocks.start()  # running before the warm-up, so that it samples the whole timed region
     for _ in range(K + 1 + args.warmup):
         M.mot_step(s.h, waves, B, None, stream)
     info0 = M.mot_get_info(s.h)
@@ -293,10 +331,9 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    clocks = Clocks(local)
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.begin()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -304,6 +341,7 @@ def run_ours(args):
         M.mot_step(s.h, waves, B, None, stream)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks.end()
     barrier()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
