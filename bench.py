@@ -105,28 +105,32 @@ def parse_clock_csv(lines, t_begin=None, t_end=None, slack=0.25):
     """Clock record of a region from nvidia-smi CSV lines (timestamp, index,
     clocks.sm, clocks.max.sm, power.draw, clocks_event_reasons.active and the
     four reasons of CLOCK_REASONS): median SM clock and the active reasons of
-    the samples taken within [t_begin - slack, t_end + slack] (host epoch
-    seconds; no window: every sample)."""
-    sm, smax, reasons, n_all = [], [], set(), 0
+    the samples stamped within [t_begin - slack, t_end + slack] (host epoch
+    seconds). With no window, or no sample stamped inside it (e.g. a timestamp
+    format this parser does not read), every sample counts and
+    "in_region_only" is false."""
+    rows = []
     for line in lines:
         p = [x.strip() for x in line.split(",")]
         if len(p) < 10:
             continue
         try:
-            ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
             f_sm, f_max = float(p[2]), float(p[3])
         except ValueError:
             continue
-        n_all += 1
-        if t_begin is not None and not (t_begin - slack <= ts <= t_end + slack):
-            continue
-        sm.append(f_sm)
-        smax.append(f_max)
-        for nm, v in zip(CLOCK_REASONS, p[6:10]):
-            if v.lower().startswith("active"):
-                reasons.add(nm)
-    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-            "samples": len(sm), "samples_outside_region": n_all - len(sm), "reasons": sorted(reasons)}
+        try:
+            ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        act = {nm for nm, v in zip(CLOCK_REASONS, p[6:10]) if v.lower().startswith("active")}
+        rows.append((ts, f_sm, f_max, act))
+    inside = [r for r in rows if t_begin is not None and r[0] is not None and
+              t_begin - slack <= r[0] <= t_end + slack]
+    use = inside if inside else rows
+    return {"sm_mhz": statistics.median(r[1] for r in use) if use else None,
+            "sm_max_mhz": max(r[2] for r in use) if use else None,
+            "samples": len(use), "samples_outside_region": len(rows) - len(use),
+            "in_region_only": bool(inside), "reasons": sorted(set().union(*[r[3] for r in use])) if use else []}
 
 
 class Clocks:

@@ -23,3 +23,38 @@ def test_clock_record_keeps_only_samples_in_region():
     assert rec["reasons"] == []
     every = bench.parse_clock_csv(lines)
     assert every["samples"] == 5 and every["reasons"] == ["hw_slowdown"]
+
+
+def test_clock_record_without_readable_stamps_keeps_every_sample():
+    lines = ["Thu Dec  3 10:00:00 2026, 0, 1980, 2070, 900.00, 0x0, Not Active, Not Active, Not Active, Active",
+             "Thu Dec  3 10:00:01 2026, 0, 2070, 2070, 900.00, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    rec = bench.parse_clock_csv(lines, 0.0, 1.0)
+    assert rec["samples"] == 2 and not rec["in_region_only"]
+    assert rec["sm_mhz"] == 2025 and rec["reasons"] == ["sw_power_cap"]
+
+
+def test_sampler_process_end_to_end(tmp_path, monkeypatch):
+    """Clocks.start/begin/end/stop against a stand-in nvidia-smi that prints
+    one stamped sample every 0.2 s (SM clock 2070 MHz, no reason active)."""
+    import os
+    import sys
+    import time
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!" + sys.executable + "\n"
+        "import datetime, sys, time\n"
+        "while True:\n"
+        "    t = datetime.datetime.now().strftime('%Y/%m/%d %H:%M:%S.%f')[:-3]\n"
+        "    print(f'{t}, 0, 2070, 2070, 950.00, 0x0, Not Active, Not Active, Not Active, Not Active', flush=True)\n"
+        "    time.sleep(0.2)\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+    c = bench.Clocks(0)
+    c.start()
+    time.sleep(0.3)
+    c.begin()
+    time.sleep(1.0)
+    c.end()
+    rec = c.stop()
+    assert rec["in_region_only"] and 4 <= rec["samples"] <= 8
+    assert rec["sm_mhz"] == 2070 and rec["reasons"] == [] and abs(rec["region_s"] - 1.0) < 0.2
