@@ -225,6 +225,36 @@ def torus(R: float = 1.0, r: float = 0.3, nu: int = 64, nv: int = 24) -> Mesh:
     return build_edges(m)
 
 
+def uv_sphere(n_lon: int = 32, n_bands: int = 25, radius: float = 1.0) -> Mesh:
+    """Latitude-longitude sphere: n_lon meridians, n_bands bands between the
+    poles (n_bands - 1 vertex rings plus the two poles), the polar bands as
+    fans and every other band's quads split along the same diagonal:
+    2 n_lon (n_bands - 1) triangles, n_lon (n_bands - 1) + 2 vertices. With
+    32 x 25 these are the counts of the unit-sphere mesh of the paper's
+    late-time experiment (1536 triangles, 770 vertices, 2304 edges)."""
+    th = np.pi * np.arange(1, n_bands) / n_bands          # colatitudes of the rings
+    ph = 2 * np.pi * np.arange(n_lon) / n_lon
+    ring = np.stack([np.outer(np.sin(th), np.cos(ph)), np.outer(np.sin(th), np.sin(ph)),
+                     np.outer(np.cos(th), np.ones(n_lon))], axis=-1).reshape(-1, 3)
+    verts = np.vstack([[0.0, 0.0, 1.0], ring, [0.0, 0.0, -1.0]]) * radius
+    north, south = 0, len(verts) - 1
+
+    def vid(b, j):  # vertex j of ring b (b = 0 .. n_bands - 2)
+        return 1 + b * n_lon + (j % n_lon)
+
+    tris = []
+    for j in range(n_lon):
+        tris.append((north, vid(0, j), vid(0, j + 1)))
+        tris.append((south, vid(n_bands - 2, j + 1), vid(n_bands - 2, j)))
+        for b in range(n_bands - 2):
+            a, bb, c, d = vid(b, j), vid(b + 1, j), vid(b + 1, j + 1), vid(b, j + 1)
+            tris.append((a, bb, c))
+            tris.append((a, c, d))
+    tris = _orient_outward(verts, np.array(tris, dtype=np.int64), lambda cen: np.zeros_like(cen))
+    m = Mesh(verts, tris.astype(np.int32), name=f"uvsphere{n_lon}x{n_bands}")
+    return build_edges(m)
+
+
 def cube(side: float = 2.0, n: int = 24) -> Mesh:
     """Axis-aligned cube centred at the origin with an n x n quad grid per face,
     every quad split along a fixed diagonal (12 n^2 triangles)."""

@@ -25,3 +25,22 @@ def pr1_ops():
 def pr1_system(pr1_ops):
     from oracle import mot as O
     return O.build_system(pr1_ops)
+
+
+def _golden_rows(name):
+    path = os.path.join(ROOT, "tests", "golden", name)
+    return [ln.split() for ln in open(path) if ln.strip() and not ln.lstrip().startswith("#")]
+
+
+def golden_table(name):
+    """Rows of a table the paper prints, from tests/golden/<name> (the file cites its passage)."""
+    return _golden_rows(name)
+
+
+def golden_values(name):
+    """key -> value (float, or tuple of floats) from tests/golden/<name> (the file cites its passage)."""
+    out = {}
+    for r in _golden_rows(name):
+        vals = tuple(float(x) for x in r[1:])
+        out[r[0]] = vals[0] if len(vals) == 1 else vals
+    return out
