@@ -224,8 +224,10 @@ int mot_step(mot_handle* h, const mot_wave* waves, int B, double* w_out, void* s
 int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, double* w_out, void* stream);
 
 /*
- * March n scatterers of uneven sizes n_steps each, concurrently (the batched
- * uneven-scatterer run). Scatterer i is marched as by
+ * March n scatterers of uneven sizes n_steps each, concurrently. The paper
+ * marches one scatterer at a time (Section V-A, Eq. (MOT)); the scatterers
+ * here are independent problems, each the same march. Scatterer i is marched
+ * as by
  *   mot_run(hs[i], n_steps, waves[i], B[i], w_out ? w_out[i] : NULL, .)
  * on a stream of its own driven by a host thread of its own: each stream
  * starts after the work already queued on `stream` and `stream` waits for all
