@@ -48,6 +48,23 @@ def test_pr1_full_march(M, pr1_ops, pr1_system):
     assert rel(W[:, :ne], ref[:, :ne]) < TOL and rel(W[:, ne:], ref[:, ne:]) < TOL
 
 
+@pytest.mark.parametrize("cdt", [5.0, 500.0])
+def test_large_timestep_parity(M, cdt):
+    """The large-timestep regime the rescaling is for (Section IV-B): PR1 mesh
+    at c dt = 5 and 500 (k_max = 1: one stored history lag, the degenerate end
+    of the method), pulse inside the run, 200 steps; loop-part (u) and
+    star-part (v) unknowns both within 1e-10 of the oracle's peak."""
+    ops = assemble(MS.icosphere(1), 2.0, 1.0, cdt)
+    assert ops.kmax == 1
+    exc = MS.single_wave(cdt, 30, 60)
+    n = 200
+    W = M.Solver(ops).run(exc, n)[:, 0].reshape(n, -1)
+    ref = O.march(O.build_system(ops), exc, n)
+    assert rel(W, ref) < TOL
+    ne = ops.ne
+    assert rel(W[:, :ne], ref[:, :ne]) < TOL and rel(W[:, ne:], ref[:, ne:]) < TOL
+
+
 @pytest.fixture(scope="module")
 def l2_case():
     ops = assemble(MS.icosphere(2), 3.0, 1.0, 0.3)
