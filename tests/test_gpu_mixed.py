@@ -109,3 +109,28 @@ def test_mixed_save_load_state_resumes_exactly(M, torus_small):
     M.mot_load_state(b.h, state)
     W2 = b.run(exc, 15)
     assert np.array_equal(W1, W2)
+
+
+def test_small_cube_regime(M):
+    """The cube configuration's regime at a size the oracle marches in
+    seconds: non-smooth cube (side 2, 6 cells per edge: 432 triangles, 648
+    edges), eps_r = 6, c dt = 0.25 (k_max = 34, 35 history lags). FP64, one
+    wave, within 1e-10; mixed, 64 waves (tensor-core history), sampled waves
+    within 1e-6 -- both against the oracle over 160 steps (pulse inside)."""
+    import math
+    ops = assemble(MS.cube(2.0, 6), 6.0, 1.0, 0.25)
+    assert ops.kmax == 34
+    S = O.build_system(ops)
+    r = math.sqrt(3.0)
+    n = 160
+    one = MS.single_wave(0.25, 30, 60, r_obj=r)
+    W1 = M.Solver(ops).run(one, n)[:, 0].reshape(n, -1)
+    e64 = rel(W1, O.march(S, one, n))
+    batch = MS.fibonacci_batch(64, 0.25, w_steps=30, t0_steps=60, r_obj=r)
+    s = M.Solver(ops, precision=M.MOT_PREC_MIXED)
+    W = s.run(batch, n)
+    assert s.info()["hist_kernel"] == 2
+    errs = [rel(W[:, b].reshape(n, -1), O.march(S, batch, n, b=b)) for b in (0, 29, 63)]
+    print(f"cube 6/edge: FP64 rel err {e64:.3e}; mixed B=64 rel errs", ["%.3e" % e for e in errs])
+    assert e64 < 1e-10
+    assert max(errs) < TOL_MIXED
