@@ -188,27 +188,32 @@ class Clocks:
 
 # DRAM bytes (read + write) of one full-depth history launch, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel and
-# workload, with the SHA-1 of the device part of the kernel source they were
-# taken on (kernel_source_sha): a changed kernel reports null until the
-# counters are taken again.
+# workload, with the SHA-1 of the device code of the kernel source they were
+# taken on (kernel_source_sha: comments and the host launch code excluded): a
+# changed kernel reports null until the counters are taken again.
 TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:k_hist_tc -s 56 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline
-    ("k_hist_tc", "torus64x24"): (47718425000 + 231234304, "11ad31f2397dc8a5589a6358558dbbb7709989bc"),
+    ("k_hist_tc", "torus64x24"): (47718425000 + 231234304, "b1cf639947bd1b231c71c62365fa2df7f5a3c7b2"),
 }
 
 
 def kernel_source_sha(name):
-    """SHA-1 of the device part of a kernel source file: its text before the
-    host launch code (the first line that opens `namespace mot {`), so that
-    edits of the host side alone keep the measured counters."""
+    """SHA-1 of the device code of a kernel source file: its text before the
+    host launch code (the first line that opens `namespace mot {`), with
+    comments removed and whitespace collapsed, so that edits of the host side
+    or of comments alone keep the measured counters."""
     import hashlib
+    import re
     p = os.path.join(ROOT, "paper_2510_07989_gb300", "csrc", name)
     if not os.path.exists(p):
         return None
-    src = open(p, "rb").read()
-    cut = src.find(b"\nnamespace mot {")
-    return hashlib.sha1(src if cut < 0 else src[:cut]).hexdigest()
+    src = open(p, encoding="utf-8").read()
+    cut = src.find("\nnamespace mot {")
+    code = src if cut < 0 else src[:cut]
+    code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+    code = re.sub(r"//[^\n]*", " ", code)
+    return hashlib.sha1(" ".join(code.split()).encode()).hexdigest()
 
 
 def traffic_of(kernel, workload, source):

@@ -42,16 +42,18 @@
 // addresses. The windowed sums of the constant K~ tail are kept in their
 // [-v, u] form and taken as they are.
 //
-// Data movement per task: the tile's three bf16 slices, split once at set-up
-// and stored in the swizzled B layout (6 KB, contiguous), by one bulk copy
-// (cp.async.bulk, completion on an mbarrier); the coefficient rows, a gather
-// through the row block's column order, by 16-byte cp.async copies that place
-// every 16-byte piece straight into the swizzled MN-major A layout.
+// Data movement per task: the two tiles' three bf16 slices each, split once at
+// set-up and stored in the swizzled B layout (2 KB per slice, contiguous), by
+// six bulk copies (cp.async.bulk) whose bytes are added to the transaction
+// count of the stage's FULL barrier; the coefficient rows, a gather through the
+// row block's column order, by 16-byte cp.async copies that place every
+// 16-byte piece straight into the swizzled MN-major A layout, each copying
+// thread arriving on the same FULL barrier once its copies have landed.
 //
 // Warp roles (224 threads, one CTA per SM):
 //   warps 0-1  gather: coefficient rows by cp.async (each lane's arrival fires
 //              on completion of its copies, so the warps never wait for them)
-//              and the tile copy
+//              and the tile copies
 //   warp  2    TMEM allocation; lane 0 issues the MMAs
 //   warps 3-6  epilogue (TMEM -> registers, compensated sums, partial results)
 // Arrivals on a barrier are shared-memory atomics on one word: the epilogue
