@@ -409,6 +409,30 @@ static void accum_mom(double* m, double v, const double* y) {
 }
 
 /*
+ * Temporal factors of one retarded interaction with R / (c dt) = j + phi,
+ * 0 <= phi < 1 (paper Section V-A): p_0 is the unit pulse on (-dt, 0), h_0 the
+ * hat of half-width dt, and q_0 the average of h_0 over one step, q_0(s) =
+ * (1/dt) int_{s-dt}^{s} h_0 (the compatibility Eq. (hq)). The lag-k factor of
+ * a basis b is b(k dt - R/c), so lag j + i takes b((i - phi) dt):
+ *   w[0..1] = dt   h_0'  at lags j, j+1
+ *   w[2..4] = dt^2 q_0'' at lags j .. j+2
+ *   w[5..7] =      q_0   at lags j .. j+2
+ *   w[8]    =      p_0   at lag j
+ */
+void asm_time_weights(double phi, double* w) {
+    const double om = 1.0 - phi;
+    w[0] = 1.0;
+    w[1] = -1.0;
+    w[2] = 1.0;
+    w[3] = -2.0;
+    w[4] = 1.0;
+    w[5] = 0.5 * om * om;
+    w[6] = 0.5 - om * om + om;
+    w[7] = 0.5 * phi * phi;
+    w[8] = 1.0;
+}
+
+/*
  * Accumulate, for one outer point x and source triangle, the lag moments
  * mom[(k - kbase) * NMOM + slot]. Returns nothing; caller sizes the window.
  */
@@ -432,19 +456,21 @@ static void td_node(const TDCtx* C, const Node* nd, int kbase, int W, double* mo
     const double* y = nd->y;
     double wr = w * iR, idt = 1.0 / dt, idt2 = idt * idt;
     double om = 1.0 - phi;
-    /* A: h_0' (+1/dt at lag j, -1/dt at lag j+1); h_0 (1-phi, phi) */
-    accum_mom(a0 + M_TA, wr * idt, y);
-    accum_mom(a1 + M_TA, -wr * idt, y);
-    /* Ah singular: q_0'' = 1, -2, 1 (/dt^2) */
-    accum_mom(a0 + M_TH, wr * idt2, y);
-    accum_mom(a1 + M_TH, -2.0 * wr * idt2, y);
-    accum_mom(a2 + M_TH, wr * idt2, y);
+    double tw[9];
+    asm_time_weights(phi, tw);
+    /* A: h_0' at lags j, j+1 */
+    accum_mom(a0 + M_TA, wr * tw[0] * idt, y);
+    accum_mom(a1 + M_TA, wr * tw[1] * idt, y);
+    /* Ah singular: q_0'' at lags j .. j+2 */
+    accum_mom(a0 + M_TH, wr * tw[2] * idt2, y);
+    accum_mom(a1 + M_TH, wr * tw[3] * idt2, y);
+    accum_mom(a2 + M_TH, wr * tw[4] * idt2, y);
     /* Ah hypersingular: q_0 values */
-    a0[M_HH] += wr * 0.5 * om * om;
-    a1[M_HH] += wr * (0.5 - om * om + om);
-    a2[M_HH] += wr * 0.5 * phi * phi;
-    /* At: p_0 = 1 at lag j */
-    accum_mom(a0 + M_TT, wr, y);
+    a0[M_HH] += wr * tw[5];
+    a1[M_HH] += wr * tw[6];
+    a2[M_HH] += wr * tw[7];
+    /* At: p_0 at lag j */
+    accum_mom(a0 + M_TT, wr * tw[8], y);
     /* K kernels: psi = chi'/(c R^2) + chi/R^3 */
     double wk2 = w * iR2 / c, wk3 = w * iR3;
     accum_mom(a0 + M_KA, wk2 * idt + wk3 * om, y);

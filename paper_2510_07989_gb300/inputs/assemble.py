@@ -58,6 +58,8 @@ def _load():
         _lib.asm_td_sizes.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         _lib.asm_td_copy.argtypes = [ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 8
         _lib.asm_td_free.argtypes = [ctypes.c_void_p]
+        _lib.asm_time_weights.argtypes = [ctypes.c_double, ctypes.c_void_p]
+        _lib.asm_time_weights.restype = None
         _lib.asm_static.restype = ctypes.c_int
         _lib.asm_static.argtypes = ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_int, ctypes.c_void_p] + [ctypes.c_void_p] * 6 +
@@ -126,6 +128,14 @@ class Operators:
     def K(self) -> int:
         """Number of history lags: Q_k vanishes for k > k_max + 1."""
         return self.kmax + 1
+
+
+def time_weights(phi: float) -> np.ndarray:
+    """The assembler's temporal factors for R / (c dt) = j + phi (asm_time_weights):
+    [dt h_0'(lags j, j+1), dt^2 q_0''(lags j..j+2), q_0(lags j..j+2), p_0(lag j)]."""
+    w = np.zeros(9)
+    _load().asm_time_weights(float(phi), w.ctypes.data_as(ctypes.c_void_p))
+    return w
 
 
 def k_max_of(tmax: float, dt: float) -> int:

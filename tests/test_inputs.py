@@ -157,3 +157,50 @@ def test_static_single_layer_symmetry(pr1_ops):
     symmetric in (m, n): a check of the quadrature accuracy."""
     s = _lag_sum(pr1_ops.mats["TT"])
     assert np.abs(s - s.T).max() < 2e-3 * np.abs(s).max()
+
+
+def test_time_bases_against_the_paper_definitions():
+    """The assembler's temporal factors (asm_time_weights, used by the T-type
+    lag moments) against the definitions of Section V-A evaluated numerically:
+    p_0 the unit pulse on (-dt, 0), h_0 the hat of half-width dt, q_0 the
+    window average of h_0 over one step (Eq. (hq)); the lag-(j+i) factor of a
+    basis b is b((i - phi) dt). Also q_0's peak 3/4 at dt/2, its C1 continuity
+    at the knots, and the compatibility Eq. (ph) linking p_0 and h_0."""
+    from paper_2510_07989_gb300.inputs.assemble import time_weights
+    dt = 0.7
+    p0 = lambda t: 1.0 if -dt < t < 0 else 0.0
+    h0 = lambda t: max(0.0, 1.0 - abs(t) / dt)
+
+    def integral(f, a, b, knots):
+        """int_a^b f for f constant or linear between knots: midpoint rule per piece (exact)."""
+        x = [a] + sorted(k for k in knots if a < k < b) + [b]
+        return sum(f(0.5 * (x0 + x1)) * (x1 - x0) for x0, x1 in zip(x[:-1], x[1:]))
+
+    q0 = lambda s: integral(h0, s - dt, s, (-dt, 0.0, dt)) / dt
+    eps = 1e-4 * dt
+    for phi in (0.05, 0.2, 0.37, 0.5, 0.63, 0.8, 0.95):
+        w = time_weights(phi)
+        xs = [(i - phi) * dt for i in range(3)]
+        for i in range(3):  # q_0 values
+            assert abs(w[5 + i] - q0(xs[i])) < 1e-13
+        for i in range(2):  # dt h_0' (one-sided inside the linear piece)
+            d = (h0(xs[i] + eps) - h0(xs[i] - eps)) / (2 * eps)
+            assert abs(w[i] - dt * d) < 1e-9
+        for i in range(3):  # dt^2 q_0'' (inside the quadratic piece)
+            d2 = (q0(xs[i] + eps) - 2 * q0(xs[i]) + q0(xs[i] - eps)) / eps ** 2
+            assert abs(w[2 + i] - dt * dt * d2) < 1e-4
+        assert w[8] == p0(xs[0]) == 1.0 and p0(xs[1]) == 0.0
+    # peak of q_0: 3/4 at dt/2 (lag j+1 of phi = 1/2)
+    assert abs(time_weights(0.5)[6] - 0.75) < 1e-15
+    assert max(time_weights(phi)[6] for phi in np.linspace(0, 1, 201)) <= 0.75 + 1e-15
+    # C1 at the knots: the factors at phi -> 1 continue those of the next lag at phi = 0
+    lo, hi = time_weights(1 - 1e-9), time_weights(0.0)
+    assert abs(lo[6] - hi[5]) < 1e-8 and abs(lo[7] - hi[6]) < 1e-8 and abs(lo[5]) < 1e-8
+    dlo = (time_weights(1 - 1e-6) - time_weights(1 - 2e-6)) / 1e-6
+    dhi = (time_weights(1e-6) - time_weights(0.0)) / 1e-6
+    assert abs(dlo[6] - dhi[5]) < 1e-4 and abs(dlo[7] - dhi[6]) < 1e-4
+    # Eq. (ph): (1/dt) int p_i(t) p_0(t + xi) dt = h_0(i dt + xi)
+    for i in (0, 1, 2):
+        for xi in (-1.3 * dt, -0.6 * dt, 0.0, 0.25 * dt, 0.9 * dt):
+            lhs = integral(lambda t: p0(t - i * dt) * p0(t + xi), (i - 1) * dt, i * dt, (-xi, -dt - xi)) / dt
+            assert abs(lhs - h0(i * dt + xi)) < 1e-12
