@@ -414,10 +414,14 @@ static void accum_mom(double* m, double v, const double* y) {
  * hat of half-width dt, and q_0 the average of h_0 over one step, q_0(s) =
  * (1/dt) int_{s-dt}^{s} h_0 (the compatibility Eq. (hq)). The lag-k factor of
  * a basis b is b(k dt - R/c), so lag j + i takes b((i - phi) dt):
- *   w[0..1] = dt   h_0'  at lags j, j+1
- *   w[2..4] = dt^2 q_0'' at lags j .. j+2
- *   w[5..7] =      q_0   at lags j .. j+2
- *   w[8]    =      p_0   at lag j
+ *   w[0..1]   = dt   h_0'  at lags j, j+1
+ *   w[2..4]   = dt^2 q_0'' at lags j .. j+2
+ *   w[5..7]   =      q_0   at lags j .. j+2
+ *   w[8]      =      p_0   at lag j
+ *   w[9..10]  =      h_0   at lags j, j+1
+ *   w[11..13] = dt   q_0'  at lags j .. j+2
+ *   w[14..15] = (1/dt) int_{-inf}^{s} p_0, the ramp of the K~ constant tail, at lags j, j+1
+ * (the time derivative of the ramp is p_0, w[8] at lag j and 0 after).
  */
 void asm_time_weights(double phi, double* w) {
     const double om = 1.0 - phi;
@@ -430,6 +434,13 @@ void asm_time_weights(double phi, double* w) {
     w[6] = 0.5 - om * om + om;
     w[7] = 0.5 * phi * phi;
     w[8] = 1.0;
+    w[9] = om;
+    w[10] = phi;
+    w[11] = om;
+    w[12] = 2.0 * phi - 1.0;
+    w[13] = -phi;
+    w[14] = om;
+    w[15] = 1.0;
 }
 
 /*
@@ -455,8 +466,7 @@ static void td_node(const TDCtx* C, const Node* nd, int kbase, int W, double* mo
     double* a2 = a1 + NMOM;
     const double* y = nd->y;
     double wr = w * iR, idt = 1.0 / dt, idt2 = idt * idt;
-    double om = 1.0 - phi;
-    double tw[9];
+    double tw[16];
     asm_time_weights(phi, tw);
     /* A: h_0' at lags j, j+1 */
     accum_mom(a0 + M_TA, wr * tw[0] * idt, y);
@@ -473,13 +483,14 @@ static void td_node(const TDCtx* C, const Node* nd, int kbase, int W, double* mo
     accum_mom(a0 + M_TT, wr * tw[8], y);
     /* K kernels: psi = chi'/(c R^2) + chi/R^3 */
     double wk2 = w * iR2 / c, wk3 = w * iR3;
-    accum_mom(a0 + M_KA, wk2 * idt + wk3 * om, y);
-    accum_mom(a1 + M_KA, -wk2 * idt + wk3 * phi, y);
-    accum_mom(a0 + M_KH, wk2 * idt2 + wk3 * om * idt, y);
-    accum_mom(a1 + M_KH, -2.0 * wk2 * idt2 + wk3 * (2.0 * phi - 1.0) * idt, y);
-    accum_mom(a2 + M_KH, wk2 * idt2 - wk3 * phi * idt, y);
-    accum_mom(a0 + M_KTD, wk2 + wk3 * om * dt, y);
-    accum_mom(a1 + M_KTS, wk3 * dt, y);
+    /* K with h_0 (A), q_0 (Ah) and the ramp of the K~ tail: chi' / (c R^2) + chi / R^3 */
+    accum_mom(a0 + M_KA, wk2 * tw[0] * idt + wk3 * tw[9], y);
+    accum_mom(a1 + M_KA, wk2 * tw[1] * idt + wk3 * tw[10], y);
+    accum_mom(a0 + M_KH, wk2 * tw[2] * idt2 + wk3 * tw[11] * idt, y);
+    accum_mom(a1 + M_KH, wk2 * tw[3] * idt2 + wk3 * tw[12] * idt, y);
+    accum_mom(a2 + M_KH, wk2 * tw[4] * idt2 + wk3 * tw[13] * idt, y);
+    accum_mom(a0 + M_KTD, wk2 * tw[8] + wk3 * tw[14] * dt, y);
+    accum_mom(a1 + M_KTS, wk3 * tw[15] * dt, y);
 }
 
 typedef struct {

@@ -132,8 +132,9 @@ class Operators:
 
 def time_weights(phi: float) -> np.ndarray:
     """The assembler's temporal factors for R / (c dt) = j + phi (asm_time_weights):
-    [dt h_0'(lags j, j+1), dt^2 q_0''(lags j..j+2), q_0(lags j..j+2), p_0(lag j)]."""
-    w = np.zeros(9)
+    [dt h_0'(lags j, j+1), dt^2 q_0''(lags j..j+2), q_0(lags j..j+2), p_0(lag j),
+     h_0(lags j, j+1), dt q_0'(lags j..j+2), ramp int p_0 / dt (lags j, j+1)]."""
+    w = np.zeros(16)
     _load().asm_time_weights(float(phi), w.ctypes.data_as(ctypes.c_void_p))
     return w
 

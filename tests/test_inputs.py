@@ -160,8 +160,8 @@ def test_static_single_layer_symmetry(pr1_ops):
 
 
 def test_time_bases_against_the_paper_definitions():
-    """The assembler's temporal factors (asm_time_weights, used by the T-type
-    lag moments) against the definitions of Section V-A evaluated numerically:
+    """The assembler's temporal factors (asm_time_weights, every temporal factor
+    of its lag moments) against the definitions of Section V-A evaluated numerically:
     p_0 the unit pulse on (-dt, 0), h_0 the hat of half-width dt, q_0 the
     window average of h_0 over one step (Eq. (hq)); the lag-(j+i) factor of a
     basis b is b((i - phi) dt). Also q_0's peak 3/4 at dt/2, its C1 continuity
@@ -190,6 +190,13 @@ def test_time_bases_against_the_paper_definitions():
             d2 = (q0(xs[i] + eps) - 2 * q0(xs[i]) + q0(xs[i] - eps)) / eps ** 2
             assert abs(w[2 + i] - dt * dt * d2) < 1e-4
         assert w[8] == p0(xs[0]) == 1.0 and p0(xs[1]) == 0.0
+        for i in range(2):  # h_0 values
+            assert abs(w[9 + i] - h0(xs[i])) < 1e-14
+        for i in range(3):  # dt q_0'
+            d = (q0(xs[i] + eps) - q0(xs[i] - eps)) / (2 * eps)
+            assert abs(w[11 + i] - dt * d) < 1e-8
+        for i in range(2):  # the ramp of the K~ tail, (1/dt) int_{-inf}^{x} p_0
+            assert abs(w[14 + i] - integral(p0, -3 * dt, xs[i], (-dt, 0.0)) / dt) < 1e-14
     # peak of q_0: 3/4 at dt/2 (lag j+1 of phi = 1/2)
     assert abs(time_weights(0.5)[6] - 0.75) < 1e-15
     assert max(time_weights(phi)[6] for phi in np.linspace(0, 1, 201)) <= 0.75 + 1e-15
