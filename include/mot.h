@@ -21,6 +21,9 @@
  *     crosses this boundary. mot_last_error() returns a message for the last
  *     failing call on a handle.
  *   - A handle is not thread safe; calls on one handle must be serialised.
+ *     Distinct handles may be used from different host threads at once (the
+ *     library keeps no shared mutable state besides per-device kernel
+ *     attributes set once; mot_run_many relies on this).
  */
 #ifndef MOT_H
 #define MOT_H
@@ -212,7 +215,9 @@ int mot_load_operators(mot_handle* h, const mot_operators* ops);
 int mot_set_frequencies(mot_handle* h, int n_freq, const double* omega);
 
 /*
- * Advance one MOT step for B plane waves (B <= 64, fixed after the first
+ * Advance one MOT step (Eq. (MOT): right-hand side of Section V-C, history
+ * sum over the lags, Q_0 solve, loop/star ring update, current recovery of
+ * Eq. (dis_jm)) for B plane waves (B <= 64, fixed after the first
  * step until mot_reset). w_out (nullable) receives w_i as [B][2][ne];
  * host or device memory (detected). stream: a cudaStream_t or NULL for the
  * default stream. Errors: MOT_ENOCONV (GMRES/CG limit hit; w_i is the last
