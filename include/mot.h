@@ -22,8 +22,9 @@
  *     failing call on a handle.
  *   - A handle is not thread safe; calls on one handle must be serialised.
  *     Distinct handles may be used from different host threads at once (the
- *     library keeps no shared mutable state besides per-device kernel
- *     attributes set once; mot_run_many relies on this).
+ *     library's only shared mutable state is per-device kernel attributes,
+ *     set once, and the staging array of mot_fields_noalloc, whose calls the
+ *     caller serialises; mot_run_many relies on this).
  */
 #ifndef MOT_H
 #define MOT_H
