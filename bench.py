@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--workload", default="torus64x24", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=8,
+                    help="timed steps of the FP64 plain arm measured beside the mixed one (0: skip it)")
     return ap.parse_args()
 
 
@@ -82,6 +84,18 @@ def throughput(world, B, steps, ms):
     return world * B * steps / (ms / 1e3)
 
 
+def make_waves(name, rank=0, t0_steps=240.0):
+    """The workload's plane waves (the paper's width w = 120 c dt) with the
+    pulse peak at the origin at t0 = t0_steps dt; rank r draws its
+    polarisations from seed 20251007 + r."""
+    from paper_2510_07989_gb300.inputs import meshes as MS
+    build_mesh, eps_r, dt, B, aopt = WORKLOADS[name]
+    r_obj = float(np.linalg.norm(build_mesh(MS).verts, axis=1).max())
+    if B == 1:
+        return MS.single_wave(dt, t0_steps=t0_steps, r_obj=r_obj)
+    return MS.fibonacci_batch(B, dt, seed=20251007 + rank, t0_steps=t0_steps, r_obj=r_obj)
+
+
 def make_workload(name, rank=0):
     from paper_2510_07989_gb300.inputs import meshes as MS
     from paper_2510_07989_gb300.inputs.assemble import assemble
@@ -90,12 +104,7 @@ def make_workload(name, rank=0):
     t = time.time()
     ops = assemble(mesh, eps_r, 1.0, dt, **aopt)
     t_asm = time.time() - t
-    r_obj = float(np.linalg.norm(mesh.verts, axis=1).max())
-    if B == 1:
-        exc = MS.single_wave(dt, r_obj=r_obj)
-    else:
-        exc = MS.fibonacci_batch(B, dt, seed=20251007 + rank, r_obj=r_obj)
-    return ops, exc, t_asm
+    return ops, make_waves(name, rank), t_asm
 
 
 CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -235,35 +244,23 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def cpu_baseline(ops, exc, seconds=20.0):
-    """The product-form FP64 oracle, as it stands, on a bounded sample: full-
-    depth MOT steps for one right-hand side on seeded history."""
+def oracle_one_step(ops, exc, b, hist, i):
+    """The product-form FP64 oracle, as it stands, computes MOT step i of wave b
+    from the GPU's own previous steps hist[j] = w_j (canonical [u; v], j < i);
+    returns (w_i, seconds of the step, seconds of the oracle set-up)."""
     from oracle import product as P
     t = time.time()
     sysP = P.ProductSystem(ops)
     t_setup = time.time() - t
     ne = ops.ne
-    K = ops.kmax + 1
-    rng = np.random.default_rng(7)
-    n_hist = K + 4
-    L = np.zeros((n_hist + 8, 2 * ne))
-    S = np.zeros((n_hist + 8, 2 * ne))
-    for j in range(1, n_hist):
-        w = rng.standard_normal(2 * ne) * 1e-3
-        L[j], S[j] = sysP.split(w)
-    steps = 0
+    L = np.zeros((i + 1, 2 * ne))
+    S = np.zeros((i + 1, 2 * ne))
+    for j, w in hist.items():
+        if j < i:
+            L[j], S[j] = sysP.split(w)
     t0 = time.time()
-    i = n_hist
-    while steps < 1 or (time.time() - t0 < seconds and steps < 4):
-        w = sysP.step(exc, 0, i, L, S)
-        L[i], S[i] = sysP.split(w)
-        i += 1
-        steps += 1
-    el = time.time() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": steps / el, "unit": "RHS·steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} full-depth MOT step(s) x 1 RHS of the same workload (product-form FP64 oracle, "
-                      f"seeded history, setup {t_setup:.0f} s excluded)"}
+    w = sysP.step(exc, b, i, L, S)
+    return w, time.time() - t0, t_setup
 
 
 def run_reference(args):
@@ -306,33 +303,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
-    import torch
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
-    from paper_2510_07989_gb300 import mot as M
-    from paper_2510_07989_gb300.build import build
-    if rank == 0:
-        build()
-    if world > 1:
-        torch.distributed.barrier()
-    M.load_library()
-    ops, exc, t_asm = make_workload(args.workload, rank)
+def march_arm(M, torch, ops, exc, args, local, world, precision, steps, warmup, clocks=None, keep_waves=()):
+    """One measured arm: K + 1 + warmup untimed steps (full-depth history), then
+    `steps` steps timed with CUDA events on the launching stream (barrier +
+    synchronize on both sides), then `steps` more through the same public call
+    with host buffers (waves in, w_i out every step) timed end to end. The
+    waves' pulse must be centred in the timed window by the caller."""
     B = exc.B
-    prec = M.MOT_PREC_MIXED if args.precision == "mixed" else M.MOT_PREC_FP64
+    K = ops.kmax + 1
+    kw = dict(device=local, timing=1, precision=precision)
+    if precision == M.MOT_PREC_FP64:
+        kw["fp64_precond"] = 1
     t = time.time()
-    s = M.Solver(ops, device=local, timing=1, precision=prec)
+    s = M.Solver(ops, **kw)
     t_load = time.time() - t
     waves = M.mot_waves(exc)
     stream = torch.cuda.current_stream()
-    K = ops.kmax + 1
-    # fill the history to full depth, then the requested warm-up
-    clocks = Clocks(local)
-    clocks.start()  # running before the warm-up, so that it samples the whole timed region
-    for _ in range(K + 1 + args.warmup):
+    for _ in range(K + 1 + warmup):
         M.mot_step(s.h, waves, B, None, stream)
     info0 = M.mot_get_info(s.h)
 
@@ -342,36 +329,41 @@ def run_ours(args):
 
     barrier()
     torch.cuda.synchronize()
-    clocks.begin()
+    if clocks:
+        clocks.begin()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         M.mot_step(s.h, waves, B, None, stream)
     ev1.record(stream)
     torch.cuda.synchronize()
-    clocks.end()
+    if clocks:
+        clocks.end()
     barrier()
-    ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     info1 = M.mot_get_info(s.h)
-    # end to end through the public API with host buffers: waves in (H2D) and
-    # w_i out (D2H) every step, inside the timed region
     host_out = torch.empty((B, 2, ops.ne), dtype=torch.float64).pin_memory()
+    kept = {b: {} for b in keep_waves}
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         M.mot_step(s.h, waves, B, host_out.numpy(), stream)
+        if kept:
+            for b in keep_waves:
+                kept[b][len(kept[b])] = host_out.numpy()[b].reshape(-1).copy()
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    ms_max, e2e_ms_max = reduce_max([ms, e2e_s * 1e3], world)
-    value = throughput(world, B, args.steps, ms_max)
-    e2e_value = throughput(world, B, args.steps, e2e_ms_max)
-    if rank != 0:
-        return
-    peaks, how = measured_peaks()
+    last_step = M.mot_get_info(s.h)["step"]
+    # kept[b][n] is step last_step - steps + 1 + n
+    hist = {b: {last_step - steps + 1 + n: w for n, w in d.items()} for b, d in kept.items()}
+    return dict(s=s, ms=ms, e2e_ms=e2e_s * 1e3, info0=info0, info1=info1, t_load=t_load, last_step=last_step,
+                hist=hist, noconv=s.noconv)
+
+
+def roofline_of(info0, info1, ms_step, steps, workload, peaks, how):
     hist_launches = info1["hist_timed_launches"] - info0["hist_timed_launches"]
     hist_ms = info1["hist_timed_ms"] - info0["hist_timed_ms"]
     flops = info1["hist_flops_per_step"]
@@ -388,7 +380,7 @@ def run_ours(args):
         bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
         roof = {"kernel": "k_hist_tc", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm if achieved else None,
-                "traffic": traffic_of("k_hist_tc", args.workload, "k_tc_hist.cu"),
+                "traffic": traffic_of("k_hist_tc", workload, "k_tc_hist.cu"),
                 "peak_source": f"measured copy bandwidth ({how})",
                 "algorithmic_bytes_per_launch": hbytes, "algorithmic_flops_per_launch": flops,
                 "tensor_issued_tflops": tc_flops / (ms_l / 1e3) / 1e12 if ms_l else None,
@@ -405,7 +397,64 @@ def run_ours(args):
                 "frac": achieved / peak if achieved else None, "traffic": None, "peak_source": psrc,
                 "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": hbytes}
     roof.update({"launches_timed": hist_launches, "ms_per_launch": ms_l,
-                 "share_of_step": ms_l / (ms_max / args.steps) if ms_l else None})
+                 "share_of_step": ms_l / ms_step if ms_l else None})
+    return roof
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    from paper_2510_07989_gb300 import mot as M
+    from paper_2510_07989_gb300.build import build
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    M.load_library()
+    ops, _, t_asm = make_workload(args.workload, rank)
+    K = ops.kmax + 1
+    primary = M.MOT_PREC_MIXED if args.precision == "mixed" else M.MOT_PREC_FP64
+    # the pulse (the paper's width, w = 120 c dt) peaks at the scatterer's
+    # centre in the middle of the timed window
+    n_pre = K + 1 + args.warmup
+    exc = make_waves(args.workload, rank, n_pre + args.steps / 2.0)
+    B = exc.B
+    clocks = Clocks(local)
+    clocks.start()  # running before the warm-up, so that it samples the whole timed region
+    A = march_arm(M, torch, ops, exc, args, local, world, primary, args.steps, args.warmup, clocks,
+                  keep_waves=(0,) if world == 1 and not args.no_cpu_baseline else ())
+    ck = clocks.stop()
+    ms_max, e2e_ms_max = reduce_max([A["ms"], A["e2e_ms"]], world)
+    value = throughput(world, B, args.steps, ms_max)
+    e2e_value = throughput(world, B, args.steps, e2e_ms_max)
+    info0, info1 = A["info0"], A["info1"]
+    # the FP64 plain arm on the same workload and GPU, with the same dense
+    # Q_0^{-1} right preconditioner (formed in FP64): the ratio isolates precision
+    fp64 = None
+    if primary == M.MOT_PREC_MIXED and args.fp64_steps > 0:
+        n64 = args.fp64_steps
+        exc64 = make_waves(args.workload, rank, K + 1 + args.warmup + n64 / 2.0)
+        F = march_arm(M, torch, ops, exc64, args, local, world, M.MOT_PREC_FP64, n64, args.warmup)
+        f_ms, f_e2e = reduce_max([F["ms"], F["e2e_ms"]], world)
+        fi0, fi1 = F["info0"], F["info1"]
+        fp64 = {"value": throughput(world, B, n64, f_ms), "unit": "RHS·steps/s", "steps": n64,
+                "ms_per_step": f_ms / n64, "dtype": "f64",
+                "solver": "right-preconditioned GMRES, Q_0 in FP64 product form, M = FP64 dense Q_0^-1",
+                "gmres_iters_per_step": (fi1["gmres_iters_total"] - fi0["gmres_iters_total"]) / n64,
+                "e2e": {"value": throughput(world, B, n64, f_e2e), "unit": "RHS·steps/s",
+                        "h2d_bytes_per_step": 80 * B, "d2h_bytes_per_step": 8 * 2 * ops.ne * B},
+                "load_s": round(F["t_load"], 1), "steps_not_converged": F["noconv"],
+                "roofline": roofline_of(fi0, fi1, f_ms / n64, n64, args.workload, *measured_peaks())}
+        del F
+    if rank != 0:
+        return
+    peaks, how = measured_peaks()
+    kern = info1["hist_kernel"]
+    roof = roofline_of(info0, info1, ms_max / args.steps, args.steps, args.workload, peaks, how)
     line = {"metric": METRIC, "value": value, "unit": "RHS·steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
@@ -416,11 +465,15 @@ def run_ours(args):
                                      "FP64 refinement, FP64 CG projector)" if kern == 2 else
                                      "mixed (FP32 history tiles, dense FP32 Q_0 and left factors, FP64 sums, "
                                      "FP64 CG projector)") if args.precision == "mixed" else "fp64 plain",
-                       "history_prefill_steps": K + 1, "load_s": round(t_load, 1),
+                       "history_prefill_steps": K + 1,
+                       "pulse": "paper's Gaussian (w = 120 c dt), peak at the scatterer centre at the middle of "
+                                "the timed window (t0 = (K + 1 + warmup + steps / 2) dt)",
+                       "load_s": round(A["t_load"], 1),
                        "l2": "inputs larger than L2 (history tiles read per step %.1f GB)" % (
                            info1["tile_count"] * {2: 6144, 1: 4096, 0: 8192}[kern] / 1e9),
                        "assembly_s": round(t_asm, 1), "parallelism": f"replicas{world}",
-                       "gmres_iters_last_step": info1["last_gmres_iters"],
+                       "gmres_iters_per_step": (info1["gmres_iters_total"] - info0["gmres_iters_total"]) / args.steps,
+                       "steps_not_converged": A["noconv"],
                        "tile_fill": round(info1["tile_fill"], 3)},
             "clocks": ck,
             "e2e": {"value": e2e_value, "unit": "RHS·steps/s", "h2d_bytes_per_step": 80 * B,
@@ -432,8 +485,24 @@ def run_ours(args):
             "roofline": roof,
             "peaks": {"source": how, "hbm_gbs": peaks.get("hbm_gbs"), "bf16_tflops": peaks.get("bf16_tflops"),
                       "bf16_tflops_sustained": peaks.get("bf16_tflops_sustained")}}
+    if fp64 is not None:
+        line["fp64"] = fp64
+        line["mixed_over_fp64"] = value / fp64["value"]
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(ops, exc)
+        # one oracle step of wave 0 from the GPU's own history: the CPU baseline
+        # (timed) and the accuracy of the GPU step at the end of the e2e window
+        hist = A["hist"][0]
+        i = A["last_step"]
+        w_ref, el, t_setup = oracle_one_step(ops, exc, 0, hist, i)
+        w_gpu = hist[i]
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        line["cpu_baseline"] = {"value": 1.0 / el, "unit": "RHS·steps/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one full-depth MOT step (step {i}) x 1 RHS (wave 0) of the same "
+                                          f"workload from the GPU's own history (product-form FP64 oracle; "
+                                          f"set-up {t_setup:.0f} s excluded)"}
+        line["accuracy"] = {"step": i, "wave": 0, "vs": "product-form FP64 oracle, one step from the GPU history",
+                            "rel_err_2norm": float(np.linalg.norm(w_gpu - w_ref) / np.linalg.norm(w_ref)),
+                            "rel_err_max": float(np.abs(w_gpu - w_ref).max() / np.abs(w_ref).max())}
     print(json.dumps(line), flush=True)
 
 

@@ -74,8 +74,8 @@ typedef struct {
                               MOT_MIX_REFINE: FP64 iterative refinement of the Q_0 solve
                               MOT_MIX_PRECOND: right-preconditioned GMRES with an FP32
                                  copy of Q_0^{-1} (LU with partial pivoting at load)
-                              MOT_MIX_TC:     with MOT_MIX_HIST32 and 2B = 128 on an sm_100-family
-                                 GPU, the history contraction runs on the tensor cores
+                              MOT_MIX_TC:     with MOT_MIX_HIST32, B a multiple of 8 and an
+                                 sm_100-family GPU, the history contraction runs on the tensor cores
                                  (tcgen05): FP32 tiles and coefficients split into three
                                  bf16 slices each, FP32 accumulation, compensated sums
                               MOT_MIX_EMU64:  on an sm_100-family GPU, the FP64 dense products
@@ -84,6 +84,13 @@ typedef struct {
                                  (relative error about 2^-40 of sum |A||x|) */
     int32_t refine_sweeps; /* MOT_MIX_REFINE: FP64 residual + correction sweeps per step
                               (stops early once |r| <= gmres_tol |b|); default 1 */
+    int32_t fp64_precond;  /* MOT_PREC_FP64 only. 0 (default): GMRES on Q_0 in product form,
+                              unpreconditioned. 1: right-preconditioned GMRES, Q_0 M z = b,
+                              x = M z, with M = Q_0^{-1} formed at load in FP64 (Q_0 from the
+                              product form on unit columns, LU with partial pivoting); every
+                              product stays FP64, so the result matches the unpreconditioned
+                              solve to the GMRES tolerance while the iteration count drops to
+                              a few. Costs (2 npad)^2 doubles of device memory. */
 } mot_options;
 
 enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8, MOT_MIX_PRECOND = 16,
@@ -183,6 +190,9 @@ typedef struct {
     /* tensor-core history: tasks of one full-depth launch (each multiplies one
        gathered 32 x 2B coefficient panel by two 32 x 32 tiles) */
     int64_t hist_tc_tasks;
+    /* GMRES iterations of the Q_0 solves summed over every step since the
+       march (re)started (the refinement's correction solves excluded) */
+    int64_t gmres_iters_total;
 } mot_info;
 
 /*
@@ -256,7 +266,8 @@ int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* cons
                  double* const* w_out, void* stream);
 
 /* Recovered currents of the last step, [B][4][ne]: j loop, j star, m loop,
- * m star (Eq. (dis_jm)), host or device memory. */
+ * m star (Eq. (dis_jm)), host or device memory. Ordered after the handle's
+ * last mot_step, whatever stream that step ran on. */
 int mot_get_currents(mot_handle* h, double* out);
 
 /*
@@ -266,7 +277,8 @@ int mot_get_currents(mot_handle* h, double* out);
  *   E_inf(r) = (j k / 4 pi) [eta r x (r x N) + r x L],
  *   N = int J^(y) e^{j k r.y}, L = int M^(y) e^{j k r.y},
  * J^, M^ the exact Fourier transforms of the piecewise-constant currents.
- * E_out (host): [B][n_freq][n_dir][3] complex as (re, im) pairs.
+ * E_out (host): [B][n_freq][n_dir][3] complex as (re, im) pairs. Ordered
+ * after the handle's last mot_step, whatever stream that step ran on.
  */
 int mot_fields(mot_handle* h, const mot_wave* waves, int n_dir, const double* dirs, double* E_out);
 
@@ -282,7 +294,9 @@ int mot_fields(mot_handle* h, const mot_wave* waves, int n_dir, const double* di
  * library keeps until the process exits.
  *   Limit: 3*n_dir + 6*B*n_freq*n_dir <= 262144, else MOT_EINVAL with a message.
  *   The first call on a device looks up the array's device address (once per
- *   device); make that first call before any stream capture.
+ *   device); make that first call before any stream capture. The address is
+ *   kept for the life of the process: a device reset between calls is not
+ *   supported.
  *   All calls share the array: calls whose GPU work overlaps race on it, so the
  *   caller must serialise them. Arguments and E_out layout as for mot_fields.
  */

@@ -55,9 +55,18 @@ class ProductSystem:
             lag = np.repeat(m.k0, m.cnt) + (np.arange(m.val.size) - first)
             v = m.val[np.repeat(m.voff, m.cnt) + (np.arange(m.val.size) - first)]
             keep = lag <= lim
-            entry = dict(rows=r[keep].astype(np.int32), cols=c[keep].astype(np.int32), lag=lag[keep].astype(np.int32),
-                         val=v[keep], typ=typ, interior=interior, uses=uses, tail=None)
-            entry["lag0"] = np.nonzero(entry["lag"] == 0)[0]
+            r, c, lag, v = r[keep], c[keep], lag[keep], v[keep]
+            entry = dict(typ=typ, interior=interior, uses=uses, tail=None, lim=lim)
+            # Z_0 of the family as a sparse N_e x N_e matrix, and its lags
+            # 1..lim side by side, [Z_1 | Z_2 | ... | Z_lim] (N_e x lim N_e), so
+            # that sum_k Z_k x_{i-k} is one product with the stacked
+            # [x_{i-1}; x_{i-2}; ...]; repeated (row, column) pairs are summed
+            l0 = lag == 0
+            entry["Z0"] = sp.csr_matrix((v[l0], (r[l0], c[l0])), shape=(ne, ne))
+            h = lag >= 1
+            entry["Zh"] = (sp.csr_matrix((v[h], (r[h], (lag[h] - 1).astype(np.int64) * ne + c[h])),
+                                         shape=(ne, lim * ne)) if lim >= 1 else None)
+            del r, c, lag, v
             if m.ta is not None:
                 tr = np.repeat(np.arange(ne), np.diff(m.rowptr))
                 ok = m.ta <= ops.kmax - 1
@@ -66,6 +75,18 @@ class ProductSystem:
             self.kinds.append(entry)
 
     # -- sums over the stored families --------------------------------------
+    def _block(self, e, zu, zv, out_u, out_v):
+        """Adds the 2 x 2 block of a family to (out_u, out_v), given zu = X pu
+        and zv = X pv for the stored matrix X (T type: [[eta X, 0], [0, X / eta]];
+        K type: [[0, -X], [X, 0]]; eta of the entry's medium)."""
+        eta = self.ops.etap if e["interior"] else self.ops.eta
+        if e["typ"] == "T":
+            out_u += eta * zu
+            out_v += zv / eta
+        else:
+            out_u -= zv
+            out_v += zu
+
     def _apply(self, e, part_u, part_v, out_u, out_v, contrib_u, contrib_v):
         ops = self.ops
         eta = ops.etap if e["interior"] else ops.eta
@@ -81,20 +102,22 @@ class ProductSystem:
         with L[j], S[j] the loop/star parts (u; v) of step j (index 0 = step 0 = zero)."""
         ne = self.ne
         s = [np.zeros(ne), np.zeros(ne), np.zeros(ne), np.zeros(ne)]  # s1u, s1v, s2u, s2v
-        parts = (L, S)
+        # stacked coefficients [x_{i-1}; x_{i-2}; ...; x_{i-kmax-1}] of each part
+        # (steps before the first are zero), u and v parts apart
+        nl = self.ops.kmax + 1
+        stacks = []
+        for P in (L, S):
+            X = np.zeros((nl, 2 * ne))
+            for k in range(1, nl + 1):
+                if i - k >= 1:
+                    X[k - 1] = P[i - k]
+            stacks.append((X[:, :ne].reshape(-1), X[:, ne:].reshape(-1)))
         for e in self.kinds:
-            lag = e["lag"]
-            src = i - lag
-            ok = (lag >= 1) & (src >= 1)
-            for part, outi in e["uses"]:
-                P = parts[part]
-                idx = np.nonzero(ok)[0]
-                si, ci = src[idx], e["cols"][idx]
-                cu = e["val"][idx] * P[si, ci]
-                cv = e["val"][idx] * P[si, ne + ci]
-                ou, ov = s[2 * outi], s[2 * outi + 1]
-                sub = dict(e, rows=e["rows"][idx])
-                self._apply(sub, None, None, ou, ov, cu, cv)
+            if e["Zh"] is not None:
+                n = e["lim"] * ne
+                for part, outi in e["uses"]:
+                    xu, xv = stacks[part]
+                    self._block(e, e["Zh"] @ xu[:n], e["Zh"] @ xv[:n], s[2 * outi], s[2 * outi + 1])
             if e["tail"] is not None:
                 tr, tcol, ta, tc = e["tail"]
                 # constant tail: sum_{k=a}^{kmax-1} l_{i-k} (steps >= 1)
@@ -111,17 +134,15 @@ class ProductSystem:
         return np.concatenate([s[0], s[1]]), np.concatenate([s[2], s[3]])
 
     def lag0(self, l, sg):
+        """y1 = A_0 l + A^_0 s, y2 = A~_0 l + A_0 s (the lag-0 terms of Q_0 w)."""
         ne = self.ne
         s = [np.zeros(ne), np.zeros(ne), np.zeros(ne), np.zeros(ne)]
         parts = (l, sg)
         for e in self.kinds:
-            idx = e["lag0"]
+            Z = e["Z0"]
             for part, outi in e["uses"]:
                 P = parts[part]
-                cu = e["val"][idx] * P[e["cols"][idx]]
-                cv = e["val"][idx] * P[ne + e["cols"][idx]]
-                sub = dict(e, rows=e["rows"][idx])
-                self._apply(sub, None, None, s[2 * outi], s[2 * outi + 1], cu, cv)
+                self._block(e, Z @ P[:ne], Z @ P[ne:], s[2 * outi], s[2 * outi + 1])
         return np.concatenate([s[0], s[1]]), np.concatenate([s[2], s[3]])
 
     def split(self, w):

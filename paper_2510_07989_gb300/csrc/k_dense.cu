@@ -200,6 +200,22 @@ __global__ void k_coldot_reduce(int nchunk, int C, const double* __restrict__ pa
         out[c] = s;
     }
 }
+// r[row][c] = f[row][c] - mean over the N rows of column c (one CTA per column):
+// the consistent part of a graph-Laplacian right-hand side (see pcg_dense_prec)
+__global__ void k_demean_cols(int N, int C, const double* __restrict__ f, double* __restrict__ r) {
+    __shared__ double red[256];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int row = threadIdx.x; row < N; row += blockDim.x) s += f[(size_t)row * C + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double mean = red[0] / (double)N;
+    for (int row = threadIdx.x; row < N; row += blockDim.x) r[(size_t)row * C + c] = f[(size_t)row * C + c] - mean;
+}
 // x += a p ; r -= a q with a = num/den per column (0 if den <= 0 or the column is done)
 __global__ void k_pcg_xr(int N, int C, const double* __restrict__ num, const double* __restrict__ den,
                          const int* __restrict__ done, const double* __restrict__ p, const double* __restrict__ q,
@@ -245,7 +261,8 @@ void dense_lap_plus_j(mot_handle* h, const DCsr& L, int npd, double* A, cudaStre
 }
 
 // Preconditioned FP64 CG on a graph Laplacian L (CSR, N rows) for C columns:
-// L z = f with f orthogonal to the constants, M an FP32 copy of (L + 11^T/N)^{-1}
+// L z = f with f orthogonal to the constants up to rounding (its column mean
+// is removed first), M an FP32 copy of (L + 11^T/N)^{-1}
 // (npd x npd, npd >= N, zero padded rows). work: 5 blocks of npd x C doubles,
 // d_scal: 6*C doubles + C ints, fstage: npd*C floats. Returns iterations (or -1).
 int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const double* f, int C, double* z,
@@ -277,8 +294,11 @@ int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const 
     cudaMemsetAsync(z, 0, sizeof(double) * blk, s);
     cudaMemsetAsync(done, 0, sizeof(int) * C, s);
     cudaMemsetAsync(r, 0, sizeof(double) * blk, s);  // padded rows must be zero (finite) for M
-    cudaMemcpyAsync(r, f, sizeof(double) * (size_t)N * C, cudaMemcpyDeviceToDevice, s);
-    coldot(f, f, ff);
+    // f sums to zero only up to rounding; its mean is an inconsistent part that
+    // CG cannot reduce, sizeable when x lies almost entirely in the loop space
+    k_demean_cols<<<C, 256, 0, s>>>(N, C, f, r);
+    h->launches++;
+    coldot(r, r, ff);
     precond(r, zz);
     cudaMemcpyAsync(p, zz, sizeof(double) * blk, cudaMemcpyDeviceToDevice, s);
     coldot(r, zz, rz);

@@ -84,7 +84,8 @@ __global__ void k_spmv(int n, int C, const int* __restrict__ rp, const int* __re
 // ----------------------------------------------------------------- CG
 // Solves A z = f column by column (A SPD, or singular and consistent: the
 // Laplacians Sigma^T Sigma and Lambda^T Lambda, whose null space is the
-// constants; f = Sigma^T x / Lambda^T x is orthogonal to it). With NORMAL the
+// constants; f = Sigma^T x / Lambda^T x is orthogonal to it up to rounding,
+// and its column mean is removed before the iteration). With NORMAL the
 // operator is A2 (A x) (CGNR for the Gram matrix: A = G, A2 = G^T).
 // One CTA owns CW columns (lane % CW) and all rows; only __syncthreads is used.
 struct CsrV {
@@ -127,10 +128,25 @@ __global__ void __launch_bounds__(1024) k_cg(int N, int C, CsrV A, CsrV A2, cons
     const int row0 = warp * RPW + lane / CW;
     const int RS = (blockDim.x >> 5) * RPW;
     double part = 0.0;
+    // A graph Laplacian (not NORMAL) is singular with the constants as its null
+    // space (connected surface). Its right-hand sides (Sigma^T x, Lambda^T x) sum
+    // to zero only up to rounding; when x lies almost entirely in the other
+    // subspace, that rounding is a sizeable inconsistent part of f, which CG
+    // cannot reduce (the iteration then runs to its limit and drifts along the
+    // null space). The column mean is removed first, so the solve is the
+    // consistent one whose minimum-norm solution is the pseudo-inverse of
+    // Section IV-B applied to f.
+    double mean = 0.0;
+    if (!NORMAL) {
+        for (int row = row0; row < N; row += RS)
+            if (cv) part += f[(size_t)row * C + c];
+        mean = col_reduce<CW>(part, red, colv) / (double)N;
+        part = 0.0;
+    }
     for (int row = row0; row < N; row += RS)
         if (cv) {
             const size_t ix = (size_t)row * C + c;
-            const double v = f[ix];
+            const double v = f[ix] - mean;
             z[ix] = 0.0;
             r[ix] = v;
             p[ix] = v;

@@ -5,9 +5,11 @@
 //   s1 = sum_k (A_k l_{i-k} + A^_k s_{i-k}),  s2 = sum_k (A~_k l_{i-k} + A_k s_{i-k}),
 // stored as 32 x 32 tiles (row block x distance-sorted column block of that
 // row block). One task multiplies one tile by the 32 coefficient rows it
-// touches, for all 2B = 128 right-hand-side columns. On the tensor core a task
-// is D[m][n] += sum_k P[m][k] X[n][k] with M = 128 (columns of the coefficient
-// panel), N = 32 (tile rows), K = 32 (tile columns).
+// touches, for all 2B right-hand-side columns. On the tensor core a task is
+// D[m][n] += sum_k P[m][k] X[n][k] with M = 128 (columns of the coefficient
+// panel), N = 32 (tile rows), K = 32 (tile columns). A batch of B < 64 waves
+// (B a multiple of 8) fills the first 2B of the 128 MMA rows; the others are
+// never copied nor read back, and every column is computed as for B = 64.
 //
 // Every coefficient panel multiplies two tiles, one per output (s1, s2); a
 // task gathers the panel once and multiplies both (the missing one is a zero
@@ -316,8 +318,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_hist_tc(const uint4* __restrict__ tasks, const HistChunk* __restrict__ chunks,
               const __nv_bfloat16* __restrict__ tiles16,
               const __nv_bfloat16* __restrict__ ring16, const __nv_bfloat16* __restrict__ win16, long long step_i,
-              int R, int npad, const int* __restrict__ colidx, double eta, double etap, double* __restrict__ partial,
-              int* __restrict__ err) {
+              int R, int npad, int C2, const int* __restrict__ colidx, double eta, double etap,
+              double* __restrict__ partial, int* __restrict__ err) {
     using L = TcLayout<NS>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // swizzled operand atoms need 1 KB alignment: the launch adds 1 KB of slack
@@ -380,7 +382,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int h = 0; h < 2; h++) dofs[ro][h] = a_chunk(ro * 8 + l8, (2 * warp + h) * 4 + l3);
         int issued = 0;  // tasks whose copies were issued
         bool ok = true;
-        const size_t pstride = (size_t)npad * TC_M;  // elements of one bf16 slice of one panel
+        const size_t pstride = (size_t)npad * C2;  // elements of one bf16 slice of one panel
+        // 16-byte pieces per coefficient row (C2 / 8); a batch below 64 waves
+        // leaves the panel's upper columns uncopied (their TMEM lanes are never read)
+        const int nch = C2 >> 3;
         for (int ti = 0; ti < ntask; ti++) {
             const uint4 d = sdesc[ti];
             const int cb = pk_cb(d), k = pk_k(d), code = pk_code(d);
@@ -404,14 +409,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int part = code & 3, var = (code >> 2) & 3;
             const __nv_bfloat16* pan = part == 2 ? win16 + (size_t)k * 3 * pstride
                                                  : ring16 + (((size_t)(slot_i - k + (slot_i < k ? R : 0)) * 2 + part) * 3) * pstride;
-            const int swap = (part != 2 && var == 2) ? 8 : 0;  // [-v, u]: 64-column halves exchanged
+            const int swap = (part != 2 && var == 2) ? nch >> 1 : 0;  // [-v, u]: the u and v halves exchanged
             const uint32_t adst = sbase + s * STAGE;
 #pragma unroll
             for (int ro = 0; ro < 4; ro++) {
-                const __nv_bfloat16* row = pan + (size_t)scol[cb * T + ro * 8 + l8] * TC_M;
+                const __nv_bfloat16* row = pan + (size_t)scol[cb * T + ro * 8 + l8] * C2;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    const __nv_bfloat16* src = row + ((((2 * warp + h) * 4 + l3) ^ swap) * 8);
+                    const int mg = (2 * warp + h) * 4 + l3;
+                    if (mg >= nch) continue;
+                    const int sc = mg + swap < nch ? mg + swap : mg + swap - nch;
+                    const __nv_bfloat16* src = row + sc * 8;
 #pragma unroll
                     for (int q = 0; q < 3; q++) cp_async16(adst + q * A_SLICE + dofs[ro][h], src + (size_t)q * pstride);
                 }
@@ -478,7 +486,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int n = 0; n < 32; n++) hs0[n] = hc0[n] = hs1[n] = hc1[n] = 0.f;
         // per-column scale of each coefficient transform (u columns m < 64, v columns m >= 64)
-        const bool ucol = m < TC_M / 2;
+        const bool ucol = m < C2 / 2;
         const float xs0 = ucol ? (float)eta : (float)(1.0 / eta), xs1 = ucol ? (float)etap : (float)(1.0 / etap),
                     xs2 = ucol ? -1.f : 1.f;
         // folds buffer b (transform key) into the sums of output o
@@ -528,12 +536,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ing++;
         }
         if (ok && g >= 0) drain(g, cur);
-        double* p0 = partial + (size_t)blockIdx.x * 2 * T * TC_M + m;
-        double* p1 = p0 + (size_t)T * TC_M;
+        if (m < C2) {
+            double* p0 = partial + (size_t)blockIdx.x * 2 * T * C2 + m;
+            double* p1 = p0 + (size_t)T * C2;
 #pragma unroll
-        for (int n = 0; n < 32; n++) {
-            p0[(size_t)n * TC_M] = (double)hs0[n] + (double)hc0[n];
-            p1[(size_t)n * TC_M] = (double)hs1[n] + (double)hc1[n];
+            for (int n = 0; n < 32; n++) {
+                p0[(size_t)n * C2] = (double)hs0[n] + (double)hc0[n];
+                p1[(size_t)n * C2] = (double)hs1[n] + (double)hc1[n];
+            }
         }
     }
     tc_fence_before();
@@ -686,17 +696,17 @@ void launch_history_tc(mot_handle* h, const TaskList& tl, long long step_i, doub
         switch (history_tc_stages(h->npad)) {
             case 6:
                 k_hist_tc<6><<<tl.nchunks, TC_THREADS, TcLayout<6>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
+                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, C2, h->d_colidx, h->eta, h->etap,
                     h->d_partial, h->d_cg_iters + 2);
                 break;
             case 5:
                 k_hist_tc<5><<<tl.nchunks, TC_THREADS, TcLayout<5>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
+                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, C2, h->d_colidx, h->eta, h->etap,
                     h->d_partial, h->d_cg_iters + 2);
                 break;
             default:
                 k_hist_tc<4><<<tl.nchunks, TC_THREADS, TcLayout<4>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, h->d_colidx, h->eta, h->etap,
+                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, C2, h->d_colidx, h->eta, h->etap,
                     h->d_partial, h->d_cg_iters + 2);
         }
         if (timed) {

@@ -315,6 +315,10 @@ void apply_q0(mot_handle* h, const Work& W, const double* v, double* out, cudaSt
         }
         return;
     }
+    if (h->prec_active && h->d_Minv64) {  // FP64 right preconditioning: Q_0 (M v), M = Q_0^{-1} in FP64
+        launch_gemm_rect(h, 2 * h->npad, 2 * h->npad, h->d_Minv64, v, h->B, W.q1, s);
+        v = W.q1;  // consumed before left_factor reuses W.q1
+    }
     project_sigma(h, W, v, W.sig, s);
     launch_axpby(h, n, 1.0, v, -1.0, W.sig, W.ell, s);
     launch_variants(h, W.ell, W.kry, h->eta, h->etap, s);
@@ -388,12 +392,15 @@ int gmres(mot_handle* h, const Work& W, const double* b, double* x, bool have_x0
 }
 
 // x solves Q_0 x = rhs by right-preconditioned GMRES: Q_0 M z = rhs, x = M z,
-// with M the FP32 copy of Q_0^{-1} (rhs must not be W.r, W.pd or W.q1)
+// with M the FP32 copy of Q_0^{-1} (mixed path) or its FP64 form (FP64 path
+// with fp64_precond); rhs must not be W.r, W.pd or W.q1
 int prec_solve(mot_handle* h, const Work& W, const double* rhs, double* x, double tol, cudaStream_t s) {
     h->prec_active = true;
     int st = gmres(h, W, rhs, W.pd, false, tol, s);
     h->prec_active = false;
-    if (h->emu_Minv.a16) {
+    if (!mixed(h)) {
+        launch_gemm_rect(h, 2 * h->npad, 2 * h->npad, h->d_Minv64, W.pd, h->B, x, s);
+    } else if (h->emu_Minv.a16) {
         launch_emu_gemm(h, h->emu_Minv, W.pd, h->B, x, s);
     } else {
         launch_d2f(h, (size_t)h->npad * 2 * h->B, W.pd, h->d_xf, s);
@@ -415,7 +422,7 @@ int ensure_state(mot_handle* h, int B) {
     if (h->opt.precision == MOT_PREC_MIXED && !h->precomputing) {
         int major = 0;
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
-        h->hist_tc = mflag(h, MOT_MIX_HIST32) && mflag(h, MOT_MIX_TC) && 2 * B == 128 && major == 10 &&
+        h->hist_tc = mflag(h, MOT_MIX_HIST32) && mflag(h, MOT_MIX_TC) && B % 8 == 0 && major == 10 &&
                       history_tc_fits(h->npad) && h->hist_tc_list.packed;
         if (h->hist_tc && !h->d_tiles16) {  // operator data: kept until mot_destroy
             // ntiles + 1 tiles: the last one stays zero (the missing partner of a merged task)
@@ -494,6 +501,7 @@ void free_state(mot_handle* h) {
     h->d_gm_bnorm = nullptr;
     h->B = 0;
     h->step = 0;
+    h->gmres_iters_total = 0;
 }
 
 int check_waves(mot_handle* h, const mot_wave* waves, int B) {
@@ -583,7 +591,7 @@ int do_step(mot_handle* h, cudaStream_t s) {
     else if (i == 2)
         launch_axpby(h, n, 1.0, h->d_wprev1, 0.0, nullptr, W.x, s);
     const bool refine = mx && mflag(h, MOT_MIX_REFINE);
-    const bool prec = mx && h->d_Minvf;
+    const bool prec = (mx && h->d_Minvf) || (!mx && h->d_Minv64);
     // with refinement the reduced-precision solves only need 1e-6: each sweep gains ~6 digits
     const double tol_in = refine ? std::max(h->opt.gmres_tol, 1e-6) : h->opt.gmres_tol;
     int st = prec ? prec_solve(h, W, W.b, W.x, tol_in, s) : gmres(h, W, W.b, W.x, have_x0, tol_in, s);
@@ -619,6 +627,7 @@ int do_step(mot_handle* h, cudaStream_t s) {
         h->last_gmres_iters = gm_iters;
     }
     PEV(5);
+    h->gmres_iters_total += h->last_gmres_iters;
     std::swap(h->d_wprev1, h->d_wprev2);
     CK(cudaMemcpyAsync(h->d_wprev1, W.x, sizeof(double) * bv, cudaMemcpyDeviceToDevice, s));
     // ring slot i: variants of l_i and s_i
@@ -687,6 +696,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
         h->opt.timing = opt->timing;
         h->opt.mixed_flags = opt->mixed_flags;
         h->opt.refine_sweeps = opt->refine_sweeps;
+        h->opt.fp64_precond = opt->fp64_precond;
     }
     auto bad = [&](const char* m) {
         h->err = m;
@@ -846,6 +856,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
     CK(cudaMemcpy(h->d_face_sgn, fs.data(), sizeof(double) * 3 * h->nf, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_iperm, h->iperm.data(), sizeof(int) * h->ne, cudaMemcpyHostToDevice));
     CK(cudaMallocHost(&h->h_cg_iters, sizeof(int) * 4));
+    CK(cudaEventCreateWithFlags(&h->ev_state, cudaEventDisableTiming));
     if (h->opt.timing) {
         CK(cudaEventCreate(&h->ev0));
         CK(cudaEventCreate(&h->ev1));
@@ -1301,6 +1312,45 @@ int precompute_mixed(mot_handle* h) {
     return MOT_OK;
 }
 
+// FP64 path with fp64_precond: Q_0^{-1} in FP64 as the right preconditioner of
+// GMRES. Q_0 is assembled column by column from the FP64 product form (64 unit
+// columns per batch), factorised by LU with partial pivoting and inverted; the
+// padded rows carry the identity.
+int precompute_fp64_precond(mot_handle* h) {
+    const int Bp = 64;
+    h->precomputing = true;
+    int st = ensure_state(h, Bp);
+    if (st != MOT_OK) return st;
+    Work W = work_of(h);
+    cudaStream_t s = 0;
+    const long long n2 = 2LL * h->npad;
+    double* q0 = (double*)dalloc(h, sizeof(double) * (size_t)n2 * n2);
+    int* piv = (int*)dalloc(h, sizeof(int) * (size_t)(n2 + 1));
+    h->d_Minv64 = (double*)dalloc(h, sizeof(double) * (size_t)n2 * n2);
+    if (!q0 || !piv || !h->d_Minv64) return fail(h, MOT_EOOM, "device allocation (FP64 Q_0 factorisation)");
+    CK(cudaMemsetAsync(h->d_cg_iters, 0, 2 * sizeof(int), s));
+    for (long long J0 = 0; J0 < n2; J0 += Bp) {
+        launch_unit_cols(h, J0, n2, W.x, s);
+        apply_q0(h, W, W.x, W.w, s);
+        launch_scatter_cols(h, J0, n2, W.w, q0, n2, s);
+    }
+    dense_pad_identity(h, (int)n2, h->ne, q0, s);
+    const int bad = dense_lu(h, (int)n2, q0, piv, piv + n2, s);
+    if (bad == 0) dense_inverse_from_lu(h, (int)n2, q0, piv, h->d_Minv64, s);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    int it[2];
+    CK(cudaMemcpy(it, h->d_cg_iters, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    cudaFree(q0);
+    cudaFree(piv);
+    h->device_bytes -= (int64_t)(sizeof(double) * (size_t)n2 * n2 + sizeof(int) * (size_t)(n2 + 1));
+    free_state(h);
+    h->precomputing = false;
+    if (bad > 0) return fail(h, MOT_EINVAL, "Q_0 is singular to working precision (LU pivot breakdown)");
+    if (it[1] > 0) return fail(h, MOT_ENOCONV, "a CG solve did not converge while assembling Q_0");
+    return MOT_OK;
+}
+
 }  // namespace
 
 MOT_API int mot_load_operators(mot_handle* h, const mot_operators* ops) {
@@ -1360,6 +1410,8 @@ MOT_API int mot_load_operators(mot_handle* h, const mot_operators* ops) {
     CK(cudaMemcpy(h->d_rhs_wf, wf.data(), sizeof(double) * wf.size(), cudaMemcpyHostToDevice));
     if ((st = build_tiles(h, ops)) != MOT_OK) return st;
     if (h->opt.precision == MOT_PREC_MIXED && (st = precompute_mixed(h)) != MOT_OK) return st;
+    if (h->opt.precision == MOT_PREC_FP64 && h->opt.fp64_precond && (st = precompute_fp64_precond(h)) != MOT_OK)
+        return st;
     h->loaded = true;
     return MOT_OK;
 }
@@ -1395,6 +1447,7 @@ MOT_API int mot_step(mot_handle* h, const mot_wave* waves, int B, double* w_out,
     if ((st = upload_waves(h, waves, B, s)) != MOT_OK) return st;
     st = do_step(h, s);
     if (st != MOT_OK && st != MOT_ENOCONV) return st;
+    CK(cudaEventRecord(h->ev_state, s));
     if (w_out) {
         Work W = work_of(h);
         if (is_device_ptr(w_out)) {
@@ -1495,6 +1548,7 @@ MOT_API int mot_get_currents(mot_handle* h, double* out) {
     if (!h || !out) return MOT_EINVAL;
     if (!h->d_cur || h->step == 0) return fail(h, MOT_ESTATE, "no step taken yet");
     CK(cudaSetDevice(h->dev));
+    CK(cudaStreamWaitEvent(0, h->ev_state, 0));  // after the last step, on whatever stream it ran
     Work W = work_of(h);
     const size_t n = (size_t)h->B * 4 * h->ne;
     if (is_device_ptr(out)) {
@@ -1516,6 +1570,7 @@ MOT_API int mot_fields(mot_handle* h, const mot_wave* waves, int n_dir, const do
     double* de = (double*)dalloc(h, sizeof(double) * (size_t)h->B * h->nfreq * std::max(1, n_dir) * 6);
     if (!dd || !de) return fail(h, MOT_EOOM, "device allocation (far field)");
     CK(cudaMemcpy(dd, dirs, sizeof(double) * 3 * n_dir, cudaMemcpyHostToDevice));
+    CK(cudaStreamWaitEvent(0, h->ev_state, 0));  // the Fourier sums of the last step, on whatever stream it ran
     launch_far_field(h, n_dir, dd, de, 0);
     CK(cudaDeviceSynchronize());
     CK(cudaMemcpy(E_out, de, sizeof(double) * (size_t)h->B * h->nfreq * n_dir * 6, cudaMemcpyDeviceToHost));
@@ -1648,6 +1703,7 @@ MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
     const double vb = h->opt.precision == MOT_PREC_MIXED ? 4.0 : 8.0;
     info->hist_bytes_per_step = vb * h->hist_nnz_unique + vb * (double)h->K * 2.0 * 2.0 * h->ne * Bc;
     info->hist_tc_tasks = h->hist_tc_list.ntasks;
+    info->gmres_iters_total = h->gmres_iters_total;
     info->hist_timed_launches = h->timed_launches;
     info->hist_timed_ms = h->timed_ms;
     for (int k = 0; k < 8; k++) info->phase_ms[k] = h->phase_ms[k];
@@ -1675,7 +1731,7 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->Gt.col, h->Gt.val, h->d_T0s, h->d_T0h, h->d_rhs_x, h->d_rhs_wf, h->d_tiles,
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
                     h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
-                    h->d_LFf, h->d_Minvf, h->d_Lfinvf, h->hist_tc_list.packed, h->hist_tc_list.chunks,
+                    h->d_LFf, h->d_Minvf, h->d_Minv64, h->d_Lfinvf, h->hist_tc_list.packed, h->hist_tc_list.chunks,
                     h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16, h->d_sgws, h->d_emuws};
     emu_free(h, &h->emu_Q0);
     emu_free(h, &h->emu_LF);
@@ -1686,6 +1742,7 @@ MOT_API void mot_destroy(mot_handle* h) {
     if (h->h_cg_iters) cudaFreeHost(h->h_cg_iters);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->ev_state) cudaEventDestroy(h->ev_state);
     for (int k = 0; k < 8; k++)
         if (h->pev[k]) cudaEventDestroy(h->pev[k]);
     delete h;

@@ -147,6 +147,7 @@ struct mot_handle {
                                    // [2] tensor-core history: code of a wait that ran out (0 = none)
     int* h_cg_iters = nullptr;     // pinned
     int last_gmres_iters = 0;
+    int64_t gmres_iters_total = 0;  // since the march (re)started
     double last_gmres_resid = 0;
     int last_cg_iters = 0;
     int64_t launches = 0;
@@ -162,7 +163,7 @@ struct mot_handle {
     float* d_win32 = nullptr;      // FP32 windowed sums
     uint16_t* d_ring16 = nullptr;  // tensor-core path: bf16 slices of l and s, [R][2 parts][3 slices][npad][2B]
     uint16_t* d_win16 = nullptr;   // tensor-core path: bf16 slices of the windowed sums, [a][3 slices][npad][2B]
-    bool hist_tc = false;          // history contraction on the tensor cores (mixed path, 2B = 128)
+    bool hist_tc = false;          // history contraction on the tensor cores (mixed path, B a multiple of 8)
     double* d_Q0 = nullptr;        // dense Q_0, (2 npad)^2, interleaved (edge, component) order, FP64
     float* d_Q0f = nullptr;        // FP32 copy
     double* d_LF = nullptr;        // dense [M1 | M2], npad x 2 npad, FP64
@@ -175,6 +176,7 @@ struct mot_handle {
     unsigned char* d_emuws = nullptr;  // their per-call workspace (X slices, split-K partials)
     size_t emuws_bytes = 0;
     float* d_Minvf = nullptr;      // FP32 Q_0^{-1} (GMRES preconditioner), (2 npad)^2
+    double* d_Minv64 = nullptr;    // FP64 Q_0^{-1} (preconditioner of the FP64 path, fp64_precond)
     bool prec_active = false;      // apply_q0 computes Q_0 M v
     float* d_Lfinvf = nullptr;     // FP32 (Sigma^T Sigma + 11^T/N_f)^{-1}, nfpd x nfpd (CG preconditioner)
     int nfpd = 0;                  // N_f padded to 64
@@ -187,6 +189,10 @@ struct mot_handle {
     int refine_sweeps = 0;         // FP64 refinement sweeps used by the last step
     // CUDA-event timing of the history launches (mot_options.timing)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // recorded on the stepping stream at the end of every mot_step: the calls
+    // that read the march state on the legacy stream (currents, far field)
+    // wait for it, whatever stream the handle last stepped on
+    cudaEvent_t ev_state = nullptr;
     cudaEvent_t pev[8] = {nullptr};  // step phase boundaries
     double phase_ms[8] = {0};
     bool ev_pending = false;
@@ -217,7 +223,7 @@ void* dalloc(mot_handle* h, size_t bytes);
 void launch_history(mot_handle* h, const TaskList& tl, const double* tiles, const double* ring, const double* win,
                     const double* kry, int mode, long long step_i, double* out_s1, double* out_s2, cudaStream_t s);
 
-// tensor-core history (mixed path, 2B = 128): tiles from d_tiles32, panels from d_ring16/d_win16
+// tensor-core history (mixed path, B a multiple of 8): tiles from d_tiles16, panels from d_ring16/d_win16
 void launch_history_tc(mot_handle* h, const TaskList& tl, long long step_i, double* out_s1, double* out_s2,
                        cudaStream_t s);
 // sum of the chunk partial results of a history launch into out_s1 / out_s2

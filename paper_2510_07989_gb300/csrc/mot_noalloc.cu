@@ -11,7 +11,9 @@
 // The array (MOT_NOALLOC_FIELD_DOUBLES doubles, 2 MiB) exists on every GPU that
 // loads the library and stays there until the process exits. Its device
 // address is looked up once per device, by the first call made with that
-// device current; make that first call before any stream capture. All calls
+// device current; make that first call before any stream capture. The address
+// is kept for the life of the process, so a device reset (cudaDeviceReset)
+// between calls is not supported. All calls
 // share the array and it keeps the last call's contents; the kernel writes
 // every output element, so nothing has to be cleared, but calls whose work
 // overlaps on the GPU race on it and must be serialised by the caller.
@@ -53,9 +55,8 @@ MOT_API int mot_fields_noalloc(mot_handle* h, const mot_wave* waves, int n_dir, 
     if (!h || !E_out || n_dir < 1 || !dirs) return MOT_EINVAL;
     if (!h->d_dft || h->nfreq == 0) return mot::fail(h, MOT_ESTATE, "no Fourier sums: call mot_set_frequencies and step");
     const size_t ndirs = (size_t)3 * n_dir;
-    const size_t dir_slot = (ndirs + 31) / 32 * 32;  // keep the result 256-byte aligned
     const size_t nout = (size_t)h->B * h->nfreq * n_dir * 6;
-    if (dir_slot + nout > (size_t)MOT_NOALLOC_FIELD_DOUBLES)
+    if (ndirs + nout > (size_t)MOT_NOALLOC_FIELD_DOUBLES)
         return mot::fail(h, MOT_EINVAL,
                          "mot_fields_noalloc: 3*n_dir + 6*B*n_freq*n_dir = " + std::to_string(ndirs + nout) +
                              " doubles exceeds the fixed scratch of " + std::to_string(MOT_NOALLOC_FIELD_DOUBLES) +
@@ -65,10 +66,13 @@ MOT_API int mot_fields_noalloc(mot_handle* h, const mot_wave* waves, int n_dir, 
     double* base = nullptr;
     e = scratch_address(h->dev, &base);
     if (e != cudaSuccess) return mot::cuda_fail(h, e, "cudaGetSymbolAddress(g_field_scratch)");
-    double* d_dirs = base;
-    double* d_E = base + dir_slot;
+    double* d_E = base;             // the result first: it starts on the array's 256-byte boundary
+    double* d_dirs = base + nout;   // the directions right after it
     e = cudaMemcpy(d_dirs, dirs, sizeof(double) * ndirs, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return mot::cuda_fail(h, e, "cudaMemcpy(directions)");
+    // the Fourier sums of the last step, on whatever stream it ran
+    e = cudaStreamWaitEvent(0, h->ev_state, 0);
+    if (e != cudaSuccess) return mot::cuda_fail(h, e, "cudaStreamWaitEvent");
     mot::launch_far_field(h, n_dir, d_dirs, d_E, 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return mot::cuda_fail(h, e, "far-field kernel launch");

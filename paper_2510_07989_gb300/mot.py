@@ -36,7 +36,8 @@ class mot_mesh(ctypes.Structure):
 class mot_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("device", ctypes.c_int32), ("gmres_tol", ctypes.c_double),
                 ("gmres_maxit", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("mixed_flags", ctypes.c_int32), ("refine_sweeps", ctypes.c_int32)]
+                ("timing", ctypes.c_int32), ("mixed_flags", ctypes.c_int32), ("refine_sweeps", ctypes.c_int32),
+                ("fp64_precond", ctypes.c_int32)]
 
 
 class mot_lagmat(ctypes.Structure):
@@ -65,7 +66,8 @@ class mot_info(ctypes.Structure):
                 ("tile_count", ctypes.c_int64), ("hist_flops_per_step", ctypes.c_double),
                 ("hist_bytes_per_step", ctypes.c_double), ("hist_timed_launches", ctypes.c_int64),
                 ("hist_timed_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8),
-                ("hist_kernel", ctypes.c_int32), ("hist_tc_tasks", ctypes.c_int64)]
+                ("hist_kernel", ctypes.c_int32), ("hist_tc_tasks", ctypes.c_int64),
+                ("gmres_iters_total", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -174,14 +176,15 @@ class Handle:
 
 
 def mot_create(verts, tris, eps_r, mu_r, dt, K, precision=MOT_PREC_FP64, device=0, gmres_tol=0.0,
-               gmres_maxit=200, cg_tol=1e-14, cg_maxit=5000, timing=0, mixed_flags=0, refine_sweeps=0) -> Handle:
+               gmres_maxit=200, cg_tol=1e-14, cg_maxit=5000, timing=0, mixed_flags=0, refine_sweeps=0,
+               fp64_precond=0) -> Handle:
     """gmres_tol <= 0 selects the library default (1e-13 FP64, 1e-11 mixed)."""
     lib = load_library()
     V = _c(verts, np.float64)
     Tr = _c(tris, np.int32)
     mesh = mot_mesh(V.shape[0], V.ctypes.data, Tr.shape[0], Tr.ctypes.data)
     opt = mot_options(precision, device, gmres_tol, gmres_maxit, cg_tol, cg_maxit, int(timing), int(mixed_flags),
-                      int(refine_sweeps))
+                      int(refine_sweeps), int(fp64_precond))
     out = ctypes.c_void_p()
     code = lib.mot_create(ctypes.byref(mesh), float(eps_r), float(mu_r), float(dt), int(K), ctypes.byref(opt),
                           ctypes.byref(out))
@@ -344,6 +347,7 @@ class Solver:
         self.h = mot_create(mesh.verts, mesh.tris, ops.eps_r, ops.mu_r, ops.dt, ops.kmax + 1, **kw)
         mot_load_operators(self.h, ops)
         self.ne = mesh.ne
+        self.noconv = 0  # steps that returned MOT_ENOCONV (a GMRES or CG iteration limit)
 
     def run(self, exc, n_steps: int, keep: bool = True):
         """March n_steps for the excitation batch; returns W [n_steps][B][2][ne] (host)."""
@@ -352,7 +356,8 @@ class Solver:
         W = np.zeros((n_steps, B, 2, self.ne)) if keep else None
         out = np.zeros((B, 2, self.ne))
         for i in range(n_steps):
-            mot_step(self.h, waves, B, out if keep else None)
+            if mot_step(self.h, waves, B, out if keep else None) == MOT_ENOCONV:
+                self.noconv += 1
             if keep:
                 W[i] = out
         return W

@@ -324,3 +324,27 @@ def test_product_form_oracle_matches_dense(pr1_ops, pr1_system):
     ref = O.march(pr1_system, exc, 60)
     W = P.ProductSystem(pr1_ops).march(exc, 60)
     assert np.abs(W - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", ["torus12x6", "cube6"])
+def test_product_form_oracle_matches_dense_where_used(case):
+    """The product-form oracle is the checker of the full-size runs (torus,
+    cube); pinned against the dense oracle in those regimes: the genus-1 torus
+    (loop space with two global loops, 53 history lags, the K~ tail over many
+    lags) for 130 steps and the non-smooth cube (35 lags) for 100 steps, both
+    with the pulse inside the run, to 1e-10 of the run's peak."""
+    from oracle import product as P
+    from paper_2510_07989_gb300.inputs.assemble import assemble
+    if case == "torus12x6":
+        ops = assemble(MS.torus(1.0, 0.3, 12, 6), 4.0, 1.0, 0.1)
+        assert ops.kmax == 52
+        exc, n = MS.fibonacci_batch(2, 0.1, w_steps=30, t0_steps=60, r_obj=1.3), 130
+    else:
+        ops = assemble(MS.cube(2.0, 6), 6.0, 1.0, 0.25)
+        assert ops.kmax == 34
+        exc, n = MS.fibonacci_batch(2, 0.25, w_steps=30, t0_steps=60, r_obj=3 ** 0.5), 100
+    S = O.build_system(ops)
+    b = 1  # the second Fibonacci wave: oblique incidence, seeded polarisation
+    ref = O.march(S, exc, n, b=b)
+    W = P.ProductSystem(ops).march(exc, n, b=b)
+    assert np.abs(W - ref).max() < 1e-10 * np.abs(ref).max()

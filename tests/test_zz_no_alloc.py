@@ -49,3 +49,19 @@ def test_fields_noalloc_rejects_oversized_request(marched):
     with pytest.raises(M.MotError) as e:
         M.mot_fields_noalloc(s.h, waves, dirs, 2, 2)
     assert e.value.code == M.MOT_EINVAL and "exceeds the fixed scratch" in str(e.value)
+
+
+def test_fields_noalloc_limit_is_exact(marched):
+    """The stated limit 3*n_dir + 6*B*n_freq*n_dir <= 262144 holds to the
+    double: with B = 2 and two frequencies, 9709 directions fit (262143
+    doubles) and 9710 do not (262170)."""
+    M, s, waves = marched
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal((9710, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    got = M.mot_fields_noalloc(s.h, waves, d[:9709], 2, 2)
+    ref = M.mot_fields(s.h, waves, d[:9709], 2, 2)
+    assert np.abs(got - ref).max() <= TOL * np.abs(ref).max()
+    with pytest.raises(M.MotError) as e:
+        M.mot_fields_noalloc(s.h, waves, d, 2, 2)
+    assert e.value.code == M.MOT_EINVAL
