@@ -78,6 +78,10 @@ typedef struct {
                                  sm_100-family GPU, the history contraction runs on the tensor cores
                                  (tcgen05): FP32 tiles and coefficients split into three
                                  bf16 slices each, FP32 accumulation, compensated sums
+                              MOT_MIX_TCBULK: with MOT_MIX_TC, the bulk form of the tensor-core
+                                 history: columns in one global order (instead of sorted per
+                                 row block), coefficient panels kept pre-swizzled in 32-row
+                                 blocks and moved by bulk copies (no per-row gather)
                               MOT_MIX_EMU64:  on an sm_100-family GPU, the FP64 dense products
                                  of the step (left factor, refinement residual) run on the
                                  tensor cores as exact products of 7-bit integer slices
@@ -91,10 +95,16 @@ typedef struct {
                               product stays FP64, so the result matches the unpreconditioned
                               solve to the GMRES tolerance while the iteration count drops to
                               a few. Costs (2 npad)^2 doubles of device memory. */
+    int32_t hist_stall_test; /* testing of the failure path only; 0 (default) = off. k > 0:
+                              every tensor-core history launch withholds the copies of the
+                              k-th task of its first CTA, whose pipeline waits then give up
+                              after 1 ms; that CTA stops, drains its copies, releases TMEM
+                              and raises the error word, and mot_step returns MOT_ECUDA
+                              with the GPU context intact. */
 } mot_options;
 
 enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8, MOT_MIX_PRECOND = 16,
-       MOT_MIX_TC = 32, MOT_MIX_EMU64 = 64,
+       MOT_MIX_TC = 32, MOT_MIX_EMU64 = 64, MOT_MIX_TCBULK = 128,
        MOT_MIX_DEFAULT = MOT_MIX_HIST32 | MOT_MIX_Q032 | MOT_MIX_REFINE | MOT_MIX_PRECOND | MOT_MIX_TC |
                          MOT_MIX_EMU64 };
 

@@ -2,6 +2,13 @@
 // (sm_100 family): Y = A X with A a fixed M x K FP64 matrix of the mixed path
 // (the left factor [M1 | M2], Q_0) and X a K x N FP64 block vector.
 //
+// Method: the error-free splitting of Ozaki et al. (the "Ozaki scheme": each
+// operand written as a sum of slices whose pairwise products are exact in the
+// low-precision unit, the slice products summed in higher precision), here in
+// its integer form -- fixed-point slices of a common per-row / per-column
+// power-of-two scale, so that the tensor core's FP32 accumulation of a chunk
+// is itself exact.
+//
 // Every row of A is scaled by a power of two so that |A_ik| < 1, every column
 // of X likewise; each scaled value is split into S signed 7-bit integer
 // slices, a = sum_p a_p 2^(-6 - 7(p-1)), |a_p| <= 64, held exactly in bf16.

@@ -68,6 +68,9 @@
 #include <algorithm>
 
 #include "mot_internal.h"
+#include "tc_ptx.h"
+
+using namespace tcx;
 
 namespace {
 
@@ -86,153 +89,9 @@ constexpr int NPROD = 64, NEPI = 128;
 constexpr int TC_THREADS = NPROD + 32 + NEPI;  // 224: warps 0-1 gather, 2 MMA, 3-6 epilogue
 constexpr int TC_CHUNK = MOT_TC_CHUNK;      // tasks per CTA (staged in shared memory)
 constexpr size_t TC_SMEM_MAX = 227 * 1024;
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // bound of every wait (2 s)
 
 static_assert(NB * BUFCOLS <= TMEM_COLS, "TMEM buffers exceed the allocation");
 static_assert(STAGE % 1024 == 0, "stage alignment");
-
-// ---- PTX wrappers -----------------------------------------------------------
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Raise the barrier's expected transaction count without arriving.
-__device__ __forceinline__ void mbar_add_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase of the given parity. Returns false when the CTA
-// was told to abort or when the bound ran out (then it raises the abort flag
-// and records `code` in the global error word). The slow path (time bound,
-// abort flag) is out of line and entered only after many failed tries, so the
-// common case costs no call.
-__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                            int code) {
-    const unsigned long long t0 = gtimer();
-    for (;;) {
-        for (int i = 0; i < 64; i++)
-            if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtimer() - t0 > WAIT_NS) {
-            *abort_flag = 1;
-            atomicExch(err, code);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
-#pragma unroll 1
-    for (int i = 0; i < 4096; i++)
-        if (mbar_try(bar, parity)) return true;
-    return mbar_wait_slow(bar, parity, abort_flag, err, code);
-}
-
-// Wait used while shutting down after an abort: bounded, ignores the flag.
-__device__ __noinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity) {
-    const unsigned long long t0 = gtimer();
-    while (!mbar_try(bar, parity))
-        if (gtimer() - t0 > WAIT_NS) return;
-}
-
-__device__ __forceinline__ void fence_barrier_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-// Arrive on the mbarrier once all prior cp.async copies of this thread have
-// landed (the arrival is counted in the barrier's expected count).
-__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// D[tmem] (+)= A[smem] x B[smem]^T, bf16 inputs, FP32 accumulation.
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// Arrive once on the mbarrier when all tcgen05 operations issued so far by
-// this thread have completed.
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// 32 lanes x 32 consecutive columns of 32 bits: thread t of the warp gets
-// lane (base lane + t), columns [col, col + 32).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptors (tcgen05 format: start >> 4, LBO >> 4,
 // SBO >> 4, version 1 at bit 46, layout type at bits 61-63).
@@ -245,23 +104,12 @@ __device__ __forceinline__ uint64_t desc_a_sw128(uint32_t addr) {
     return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(4096 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
            (1ull << 46) | (2ull << 61);
 }
-// B, the tile slices, K-major with the 64-byte swizzle: rows of 32 bf16
-// (64 bytes), 8-row atoms of 512 bytes, the 16-byte chunk c of row r at chunk
-// position c ^ ((r >> 1) & 3); SBO = 512 bytes between 8-row groups (LBO is
-// not used by K-major swizzled layouts).
-__device__ __forceinline__ uint64_t desc_b_sw64(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) |
-           (4ull << 61);
-}
+// B, the tile slices: K-major with the 64-byte swizzle (desc_kmajor_sw64,
+// sw64_chunk of the shared header).
 // byte offset of the 16-byte chunk (m >> 3) of lag row k in an A slice
-__device__ __forceinline__ uint32_t a_chunk(int k, int mg) {
+__host__ __device__ __forceinline__ uint32_t a_chunk(int k, int mg) {
     return (uint32_t)((mg >> 3) * 4096 + (k >> 3) * 1024 + (k & 7) * 128 + (((mg & 7) ^ (k & 7)) << 4));
 }
-// byte offset of the 16-byte chunk kc (columns 8 kc .. 8 kc + 7) of tile row n in a B slice
-__device__ __forceinline__ uint32_t b_chunk(int n, int kc) {
-    return (uint32_t)((n >> 3) * 512 + (n & 7) * 64 + ((kc ^ ((n & 7) >> 1)) << 4));
-}
-
 // Instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, A
 // MN-major (the coefficient panel, M contiguous), B K-major (the tile), M = 128.
 __host__ __device__ constexpr uint32_t idesc_bf16(int N) {
@@ -301,26 +149,45 @@ __device__ __forceinline__ int pk_code(uint4 d) { return (int)(d.z >> 26); }
 // windowed sums (used as stored).
 __device__ __forceinline__ int task_xform(int code) { return (code & 3) == 2 ? 3 : (code >> 2) & 3; }
 
-template <int NS>
+template <int NS, bool BULK>
 struct TcLayout {
     static constexpr int NBARS = 2 * NS + 2 * NB + 1;  // + one barrier for the final MMA drain
     static constexpr size_t BARS = (size_t)NS * STAGE;
-    static constexpr size_t SLOT = BARS + ((8 * NBARS + 15) / 16) * 16;  // TMEM address, abort flag
+    static constexpr size_t SLOT = BARS + ((8 * NBARS + 15) / 16) * 16;  // TMEM address, abort flag, issued count
     static constexpr size_t DESC = SLOT + 16;                             // TC_CHUNK packed tasks (uint4)
     static constexpr size_t COLS = DESC + 16 * TC_CHUNK;                  // column order of the row block (uint16)
-    static size_t bytes(int npad) { return COLS + (((size_t)npad * 2 + 15) / 16) * 16 + 1024; }
+    // the gathered form stages the row block's column order; the bulk form has none
+    static size_t bytes(int npad) { return COLS + (BULK ? 0 : (((size_t)npad * 2 + 15) / 16) * 16) + 1024; }
     static_assert(BARS % 1024 == 0 && SLOT % 16 == 0 && DESC % 16 == 0 && COLS % 16 == 0,
                   "shared-memory regions must keep their alignment (uint4 task loads)");
 };
 
-template <int NS>
+// Element offset, in a blocked panel of the bulk form, of column m (0..127:
+// half m >> 6, column m & 63 of the half) of coefficient row r of a 32-row
+// block: each block is 8 KB, already in the MN-major 128-byte-swizzled layout
+// of the MMA's A operand (a_chunk), so one bulk copy places it in shared memory.
+__host__ __device__ __forceinline__ uint32_t blk_elem(int r, int m) {
+    return (a_chunk(r, m >> 3) >> 1) + (uint32_t)(m & 7);
+}
+
+// BULK = false (gathered form): the columns of a row block are sorted by their
+// distance from the block, and a panel's 32 coefficient rows are gathered from
+// the ring ([npad][2B] per slice) by 16-byte cp.async copies of two warps,
+// through the row block's column order staged in shared memory.
+// BULK = true (bulk form): columns in the global (Morton) order, so the panel
+// of column block cb is ring rows [32 cb, 32 cb + 32); the ring is stored in
+// 32-row blocks already swizzled ([nrb][8 KB] per slice, u in the first 64-column
+// half, v in the second), and one thread moves a stage with bulk copies: per
+// slice one 8 KB copy (or two 4 KB copies with the halves exchanged for
+// [-v, u]) and the six 2 KB tile slices, all counted in bytes on FULL.
+template <int NS, bool BULK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_hist_tc(const uint4* __restrict__ tasks, const HistChunk* __restrict__ chunks,
               const __nv_bfloat16* __restrict__ tiles16,
               const __nv_bfloat16* __restrict__ ring16, const __nv_bfloat16* __restrict__ win16, long long step_i,
               int R, int npad, int C2, const int* __restrict__ colidx, double eta, double etap,
-              double* __restrict__ partial, int* __restrict__ err) {
-    using L = TcLayout<NS>;
+              double* __restrict__ partial, int* __restrict__ err, int stall_task, unsigned long long stall_bound) {
+    using L = TcLayout<NS, BULK>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // swizzled operand atoms need 1 KB alignment: the launch adds 1 KB of slack
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
@@ -328,6 +195,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t bar0 = sbase + (uint32_t)L::BARS;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::SLOT);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* issued_slot = reinterpret_cast<int*>(tmem_slot + 2);  // tasks whose copies the gather warps issued
     uint4* sdesc = reinterpret_cast<uint4*>(smem + L::DESC);
     uint16_t* scol = reinterpret_cast<uint16_t*>(smem + L::COLS);
     // FULL: the coefficient rows (one arrival per copying thread, when its
@@ -341,14 +209,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const HistChunk ch = chunks[blockIdx.x];
+    // failure test (stall_task >= 0): the first CTA withholds the copies and
+    // arrivals of its task stall_task, and every wait of that CTA gives up
+    // after stall_bound ns, so the launch ends through the abort path
+    const bool stall_cta = stall_task >= 0 && blockIdx.x == 0;
+    const unsigned long long bound = stall_cta ? stall_bound : WAIT_NS;
     const int ntask = ch.count;  // <= TC_CHUNK
 
     // the chunk's task list and the row block's column order, staged once
     for (int i = tid; i < ntask; i += TC_THREADS) sdesc[i] = tasks[ch.first + i];
-    for (int p = tid; p < npad; p += TC_THREADS) scol[p] = (uint16_t)colidx[(size_t)ch.rb * npad + p];
+    if (!BULK)
+        for (int p = tid; p < npad; p += TC_THREADS) scol[p] = (uint16_t)colidx[(size_t)ch.rb * npad + p];
     if (tid == 0) {
         for (int s = 0; s < NS; s++) {
-            mbar_init(FULL(s), NPROD);
+            mbar_init(FULL(s), BULK ? 1 : NPROD);
             mbar_init(EMPTY(s), 1);
         }
         for (int b = 0; b < NB; b++) {
@@ -357,6 +231,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         mbar_init(DRAIN, 1);
         *abort_flag = 0;
+        *issued_slot = 0;
         fence_barrier_init();
     }
     if (warp == 2) {
@@ -368,7 +243,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < 2) {
+    if (BULK && warp < 2) {
+        // ---------------- bulk producer: one thread moves every stage ----------------
+        if (tid == 0) {
+            const int slot_i = (int)(step_i % R);
+            const size_t pslice = (size_t)npad * 128;  // elements of one slice of one ring part (all blocks)
+            int issued = 0;
+            for (int ti = 0; ti < ntask; ti++) {
+                const uint4 d = sdesc[ti];
+                const int cb = pk_cb(d), k = pk_k(d), code = pk_code(d);
+                if (step_i - k < 1) continue;
+                const int j = issued;
+                const int s = j % NS;
+                if (!mbar_wait(EMPTY(s), ((uint32_t)(j / NS) & 1u) ^ 1u, abort_flag, err, 2, bound)) break;
+                issued = j + 1;
+                *issued_slot = issued;
+                if (stall_cta && j == stall_task) continue;  // failure test: this stage is never filled
+                mbar_expect_tx(FULL(s), STAGE);  // the one arrival, with every byte of the stage
+                const uint32_t adst = sbase + s * STAGE;
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    bulk_g2s(adst + STAGE_A + (2 * q) * B_SLICE, tiles16 + ((size_t)d.x * 3 + q) * (T * T), B_SLICE,
+                             FULL(s));
+                    bulk_g2s(adst + STAGE_A + (2 * q + 1) * B_SLICE, tiles16 + ((size_t)d.y * 3 + q) * (T * T),
+                             B_SLICE, FULL(s));
+                }
+                const int part = code & 3, var = (code >> 2) & 3;
+                const __nv_bfloat16* blk =
+                    (part == 2 ? win16 + (size_t)k * 3 * pslice
+                               : ring16 + (((size_t)(slot_i - k + (slot_i < k ? R : 0)) * 2 + part) * 3) * pslice) +
+                    (size_t)cb * (T * 128);
+                if (part != 2 && var == 2) {  // [-v, u]: the v half first
+#pragma unroll
+                    for (int q = 0; q < 3; q++) {
+                        bulk_g2s(adst + q * A_SLICE, blk + q * pslice + T * 64, A_SLICE / 2, FULL(s));
+                        bulk_g2s(adst + q * A_SLICE + A_SLICE / 2, blk + q * pslice, A_SLICE / 2, FULL(s));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 3; q++) bulk_g2s(adst + q * A_SLICE, blk + q * pslice, A_SLICE, FULL(s));
+                }
+            }
+        }
+    } else if (!BULK && warp < 2) {
         // ---------------- gather: coefficient rows and the tile copy ----------------
         const int t = tid;
         const int l8 = lane & 7, l3 = lane >> 3;
@@ -384,17 +301,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool ok = true;
         const size_t pstride = (size_t)npad * C2;  // elements of one bf16 slice of one panel
         // 16-byte pieces per coefficient row (C2 / 8); a batch below 64 waves
-        // leaves the panel's upper columns uncopied (their TMEM lanes are never read)
+        // leaves the panel's upper columns uncopied (their TMEM lanes are never
+        // read). Source offsets of this lane's two pieces, as stored and with
+        // the u and v halves exchanged ([-v, u]), fixed for the whole chunk.
         const int nch = C2 >> 3;
+        int soff0[2], soff1[2];
+        bool has[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int mg = (2 * warp + h) * 4 + l3;
+            has[h] = mg < nch;
+            const int sw = mg + (nch >> 1) < nch ? mg + (nch >> 1) : mg + (nch >> 1) - nch;
+            soff0[h] = mg * 8;
+            soff1[h] = sw * 8;
+        }
         for (int ti = 0; ti < ntask; ti++) {
             const uint4 d = sdesc[ti];
             const int cb = pk_cb(d), k = pk_k(d), code = pk_code(d);
             if (step_i - k < 1) continue;
             const int j = issued;
             const int s = j % NS;
-            if (!mbar_wait(EMPTY(s), ((uint32_t)(j / NS) & 1u) ^ 1u, abort_flag, err, 2)) {
+            if (!mbar_wait(EMPTY(s), ((uint32_t)(j / NS) & 1u) ^ 1u, abort_flag, err, 2, bound)) {
                 ok = false;
                 break;
+            }
+            if (stall_cta && j == stall_task) {  // failure test: this stage is never filled
+                issued = j + 1;
+                if (t == 0) *issued_slot = issued;
+                continue;
             }
             if (t == 0) {  // slices in the order Y0 Z0 Y1 Z1 Y2 Z2; bytes added before this thread's arrival
                 mbar_add_tx(FULL(s), STAGE_B);
@@ -409,17 +343,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int part = code & 3, var = (code >> 2) & 3;
             const __nv_bfloat16* pan = part == 2 ? win16 + (size_t)k * 3 * pstride
                                                  : ring16 + (((size_t)(slot_i - k + (slot_i < k ? R : 0)) * 2 + part) * 3) * pstride;
-            const int swap = (part != 2 && var == 2) ? nch >> 1 : 0;  // [-v, u]: the u and v halves exchanged
+            const int swap = (part != 2 && var == 2) ? 1 : 0;  // [-v, u]: the u and v halves exchanged
             const uint32_t adst = sbase + s * STAGE;
 #pragma unroll
             for (int ro = 0; ro < 4; ro++) {
                 const __nv_bfloat16* row = pan + (size_t)scol[cb * T + ro * 8 + l8] * C2;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
-                    const int mg = (2 * warp + h) * 4 + l3;
-                    if (mg >= nch) continue;
-                    const int sc = mg + swap < nch ? mg + swap : mg + swap - nch;
-                    const __nv_bfloat16* src = row + sc * 8;
+                    if (!has[h]) continue;
+                    const __nv_bfloat16* src = row + (swap ? soff1[h] : soff0[h]);
 #pragma unroll
                     for (int q = 0; q < 3; q++) cp_async16(adst + q * A_SLICE + dofs[ro][h], src + (size_t)q * pstride);
                 }
@@ -427,11 +359,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // this thread's arrival on the stage fires when its copies have landed
             cp_async_arrive_noinc(FULL(s));
             issued = j + 1;
+            if (t == 0) *issued_slot = issued;
         }
-        cp_async_wait_all();
-        if (!ok && t == 0)  // let the tile copies in flight land before the CTA exits
-            for (int jj = issued > NS ? issued - NS : 0; jj < issued; jj++)
-                mbar_wait_drain(FULL(jj % NS), (uint32_t)(jj / NS) & 1u);
+        (void)ok;
+        cp_async_wait_all();  // this thread's row copies have landed
     } else if (warp == 2) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
@@ -447,20 +378,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     ing = 0;
                     cur = key;
                     const int b = g % NB;
-                    if (!mbar_wait(ACCE(b), ((uint32_t)(g / NB) & 1u) ^ 1u, abort_flag, err, 3)) break;
+                    if (!mbar_wait(ACCE(b), ((uint32_t)(g / NB) & 1u) ^ 1u, abort_flag, err, 3, bound)) break;
                     tc_fence_after();
                     dcol = tmem + (uint32_t)(b * BUFCOLS);
                 }
                 const int s = j % NS;
-                if (!mbar_wait(FULL(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 4)) break;
-                fence_proxy_async();  // coefficient rows written by cp.async (generic proxy)
+                if (!mbar_wait(FULL(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 4, bound)) break;
+                if (!BULK) fence_proxy_async();  // coefficient rows written by cp.async (generic proxy)
                 tc_fence_after();
                 const uint32_t a0 = sbase + s * STAGE, b0 = a0 + STAGE_A;
                 // K-half kk: A rows 16 kk .. 16 kk + 15 (two 1 KB row groups),
                 // B columns 16 kk .. (32 bytes into each 64-byte row)
 #pragma unroll
                 for (int kk = 0; kk < 2; kk++) {
-                    const uint64_t bd = desc_b_sw64(b0 + kk * 32);
+                    const uint64_t bd = desc_kmajor_sw64(b0 + kk * 32);
                     mma_bf16(dcol, desc_a_sw128(a0 + kk * 2048), bd, idesc_bf16(192), (ing > 0 || kk > 0) ? 1u : 0u);
                     mma_bf16(dcol + 64, desc_a_sw128(a0 + A_SLICE + kk * 2048), bd, idesc_bf16(128), 1u);
                     mma_bf16(dcol + 128, desc_a_sw128(a0 + 2 * A_SLICE + kk * 2048), bd, idesc_bf16(64), 1u);
@@ -474,7 +405,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (g >= 0) tc_commit(ACCF(g % NB));
             // TMEM is released only after every MMA of this CTA has completed
             tc_commit(DRAIN);
-            mbar_wait_drain(DRAIN, 0);
+            mbar_wait_drain(DRAIN, 0, bound);
         }
         __syncwarp();
     } else {
@@ -485,8 +416,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float hs0[32], hc0[32], hs1[32], hc1[32];  // compensated sums of s1 and s2
 #pragma unroll
         for (int n = 0; n < 32; n++) hs0[n] = hc0[n] = hs1[n] = hc1[n] = 0.f;
-        // per-column scale of each coefficient transform (u columns m < 64, v columns m >= 64)
-        const bool ucol = m < C2 / 2;
+        // per-column scale of each coefficient transform. Gathered form: panel
+        // column m is u of wave m (m < B) or v of wave m - B. Bulk form: u of
+        // wave m & 63 in the first half (m < 64), v in the second.
+        const int Bw = C2 / 2;
+        const bool ucol = BULK ? m < 64 : m < Bw;
+        const int ocol = BULK ? ((m & 63) < Bw ? (m >> 6) * Bw + (m & 63) : -1) : (m < C2 ? m : -1);
         const float xs0 = ucol ? (float)eta : (float)(1.0 / eta), xs1 = ucol ? (float)etap : (float)(1.0 / etap),
                     xs2 = ucol ? -1.f : 1.f;
         // folds buffer b (transform key) into the sums of output o
@@ -509,7 +444,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         };
         auto drain = [&](int gg, int key) -> bool {
             const int b = gg % NB;
-            if (!mbar_wait(ACCF(b), (uint32_t)(gg / NB) & 1u, abort_flag, err, 5)) return false;
+            if (!mbar_wait(ACCF(b), (uint32_t)(gg / NB) & 1u, abort_flag, err, 5, bound)) return false;
             tc_fence_after();
             __syncwarp();
             const float c = key == 0 ? xs0 : key == 1 ? xs1 : key == 2 ? xs2 : 1.f;
@@ -536,8 +471,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ing++;
         }
         if (ok && g >= 0) drain(g, cur);
-        if (m < C2) {
-            double* p0 = partial + (size_t)blockIdx.x * 2 * T * C2 + m;
+        if (ocol >= 0) {
+            double* p0 = partial + (size_t)blockIdx.x * 2 * T * C2 + ocol;
             double* p1 = p0 + (size_t)T * C2;
 #pragma unroll
             for (int n = 0; n < 32; n++) {
@@ -552,11 +487,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
     }
+    // After an abort (every role has stopped: the flag is final here), tile
+    // copies of stages the MMA thread never consumed may still be in flight:
+    // wait (bounded) for the stages of the last NS issued tasks before the
+    // CTA's shared memory is released.
+    if (tid == 0 && *abort_flag) {
+        const int issued = *issued_slot;
+        for (int jj = issued > NS ? issued - NS : 0; jj < issued; jj++)
+            mbar_wait_drain(FULL(jj % NS), (uint32_t)(jj / NS) & 1u, bound);
+    }
 }
 
 // src: npanels panels of n doubles; dst: npanels x 3 bf16 slices of n values.
-__global__ void k_split3(size_t n, int npanels, const double* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+// Blocked (bulk-form) panels: n = npad x 2B values per panel become three
+// slices of npad x 128 bf16 each, in 32-row blocks of blk_elem layout (the
+// first B columns of a row in the first half, the next B in the second; the
+// other columns stay as allocated, zero).
+__global__ void k_split3(size_t n, int npanels, int C2, int blocked, const double* __restrict__ src,
+                         __nv_bfloat16* __restrict__ dst) {
     const size_t total = n * (size_t)npanels;
+    const size_t ns = blocked ? n / C2 * 128 : n;  // elements of one slice
+    const int B = C2 / 2;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const size_t p = i / n, r = i - p * n;
         const double x = src[i];
@@ -565,10 +516,17 @@ __global__ void k_split3(size_t n, int npanels, const double* __restrict__ src, 
         const __nv_bfloat16 b = __double2bfloat16(r1);
         const double r2 = r1 - (double)__bfloat162float(b);
         const __nv_bfloat16 c = __double2bfloat16(r2);
-        __nv_bfloat16* d = dst + p * 3 * n + r;
+        size_t e = r;
+        if (blocked) {
+            const size_t row = r / C2;
+            const int m = (int)(r - row * C2);
+            const int mm = m < B ? m : 64 + m - B;
+            e = (row >> 5) * (T * 128) + blk_elem((int)(row & 31), mm);
+        }
+        __nv_bfloat16* d = dst + p * 3 * ns + e;
         d[0] = a;
-        d[n] = b;
-        d[2 * n] = c;
+        d[ns] = b;
+        d[2 * ns] = c;
     }
 }
 
@@ -586,7 +544,7 @@ __global__ void k_split_tiles(long long ntiles, const float* __restrict__ src, _
         __nv_bfloat16 a[8], b[8], c[8];
 #pragma unroll
         for (int e = 0; e < 8; e++) split3(x[e], a[e], b[e], c[e]);
-        unsigned char* d = reinterpret_cast<unsigned char*>(dst + (size_t)t * 3 * T * T) + b_chunk(r, kc);
+        unsigned char* d = reinterpret_cast<unsigned char*>(dst + (size_t)t * 3 * T * T) + sw64_chunk(r, kc);
         *reinterpret_cast<uint4*>(d) = make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]), pack2(a[6], a[7]));
         *reinterpret_cast<uint4*>(d + B_SLICE) =
             make_uint4(pack2(b[0], b[1]), pack2(b[2], b[3]), pack2(b[4], b[5]), pack2(b[6], b[7]));
@@ -596,10 +554,14 @@ __global__ void k_split_tiles(long long ntiles, const float* __restrict__ src, _
 }
 
 // bf16 slices of l and s of one ring slot, columns [u | v], from the FP64
-// ring's [-v, u] variant of each part: dst [2 parts][3 slices][npad][2B].
-__global__ void k_split_ring(int npad, int B, const double* __restrict__ ring_slot, __nv_bfloat16* __restrict__ dst) {
+// ring's [-v, u] variant of each part: dst [2 parts][3 slices][npad][2B]
+// (gathered form), or [2 parts][3 slices][npad x 128] in blk_elem blocks, u in
+// the first half and v in the second (bulk form).
+__global__ void k_split_ring(int npad, int B, int blocked, const double* __restrict__ ring_slot,
+                             __nv_bfloat16* __restrict__ dst) {
     const int C2 = 2 * B;
-    const size_t ps = (size_t)npad * C2;
+    const size_t ps = (size_t)npad * C2;                  // FP64 values of one part's variant
+    const size_t ds = blocked ? (size_t)npad * 128 : ps;  // elements of one destination slice
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < 2 * ps; i += (size_t)gridDim.x * blockDim.x) {
         const int part = (int)(i / ps);
         const size_t r = (i - part * ps) / C2;
@@ -610,10 +572,11 @@ __global__ void k_split_ring(int npad, int B, const double* __restrict__ ring_sl
         const double r1 = x - (double)__bfloat162float(a);
         const __nv_bfloat16 b = __double2bfloat16(r1);
         const double r2 = r1 - (double)__bfloat162float(b);
-        __nv_bfloat16* d = dst + (size_t)part * 3 * ps + r * C2 + m;
+        const size_t e = blocked ? (r >> 5) * (T * 128) + blk_elem((int)(r & 31), m < B ? m : 64 + m - B) : r * C2 + m;
+        __nv_bfloat16* d = dst + (size_t)part * 3 * ds + e;
         d[0] = a;
-        d[ps] = b;
-        d[2 * ps] = __double2bfloat16(r2);
+        d[ds] = b;
+        d[2 * ds] = __double2bfloat16(r2);
     }
 }
 
@@ -651,30 +614,38 @@ void launch_split_tiles(mot_handle* h, cudaStream_t s) {
 
 void launch_split_ring(mot_handle* h, int slot, cudaStream_t s) {
     const size_t bv = (size_t)h->npad * 2 * h->B;
+    const size_t slot16 = history_tc_ring_slot_elems(h);
     const int blocks = (int)std::min<size_t>((2 * bv + 255) / 256, 152 * 16);
-    k_split_ring<<<blocks, 256, 0, s>>>(h->npad, h->B, h->d_ring + (size_t)slot * 6 * bv,
-                                        reinterpret_cast<__nv_bfloat16*>(h->d_ring16) + (size_t)slot * 6 * bv);
+    k_split_ring<<<blocks, 256, 0, s>>>(h->npad, h->B, h->tc_bulk ? 1 : 0, h->d_ring + (size_t)slot * 6 * bv,
+                                        reinterpret_cast<__nv_bfloat16*>(h->d_ring16) + (size_t)slot * slot16);
     h->launches++;
 }
 
+size_t history_tc_ring_slot_elems(const mot_handle* h) {
+    // 2 parts x 3 slices of npad x 2B (gathered form) or npad x 128 (bulk form)
+    return (size_t)6 * h->npad * (h->tc_bulk ? 128 : 2 * h->B);
+}
 
-// pipeline depth: the deepest that fits next to the row block's column order
-int history_tc_stages(int npad) {
+
+// pipeline depth: the deepest that fits (next to the row block's column order
+// in the gathered form)
+int history_tc_stages(int npad, bool bulk) {
     if (npad > 65536) return 0;
-    if (TcLayout<6>::bytes(npad) <= TC_SMEM_MAX) return 6;
-    if (TcLayout<5>::bytes(npad) <= TC_SMEM_MAX) return 5;
-    if (TcLayout<4>::bytes(npad) <= TC_SMEM_MAX) return 4;
+    if (bulk) return TcLayout<5, true>::bytes(npad) <= TC_SMEM_MAX ? 5 : 4;
+    if (TcLayout<6, false>::bytes(npad) <= TC_SMEM_MAX) return 6;
+    if (TcLayout<5, false>::bytes(npad) <= TC_SMEM_MAX) return 5;
+    if (TcLayout<4, false>::bytes(npad) <= TC_SMEM_MAX) return 4;
     return 0;
 }
 
-bool history_tc_fits(int npad) { return history_tc_stages(npad) > 0; }
+bool history_tc_fits(int npad, bool bulk) { return history_tc_stages(npad, bulk) > 0; }
 
 void launch_split3(mot_handle* h, int npanels, const double* src, uint16_t* dst, cudaStream_t s) {
     const size_t n = (size_t)h->npad * 2 * h->B;
     const size_t total = n * (size_t)npanels;
     if (total == 0) return;
     const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 16);
-    k_split3<<<blocks, 256, 0, s>>>(n, npanels, src, reinterpret_cast<__nv_bfloat16*>(dst));
+    k_split3<<<blocks, 256, 0, s>>>(n, npanels, 2 * h->B, h->tc_bulk ? 1 : 0, src, reinterpret_cast<__nv_bfloat16*>(dst));
     h->launches++;
 }
 
@@ -686,29 +657,32 @@ void launch_history_tc(mot_handle* h, const TaskList& tl, long long step_i, doub
         if (timed) cudaEventRecord(h->ev0, s);
         static std::atomic<unsigned long long> attr{0};
         once_per_device(attr, h->dev, [] {
-            cudaFuncSetAttribute(k_hist_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-            cudaFuncSetAttribute(k_hist_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-            cudaFuncSetAttribute(k_hist_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+            cudaFuncSetAttribute(k_hist_tc<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+            cudaFuncSetAttribute(k_hist_tc<5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+            cudaFuncSetAttribute(k_hist_tc<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+            cudaFuncSetAttribute(k_hist_tc<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+            cudaFuncSetAttribute(k_hist_tc<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
         });
+        // failure test of the bounded waits (mot_options.hist_stall_test), off by default
+        const int stall = h->opt.hist_stall_test > 0 ? h->opt.hist_stall_test - 1 : -1;
         const uint4* pt = tl.packed;
         const auto* r16 = reinterpret_cast<const __nv_bfloat16*>(h->d_ring16);
         const auto* w16 = reinterpret_cast<const __nv_bfloat16*>(h->d_win16);
-        switch (history_tc_stages(h->npad)) {
-            case 6:
-                k_hist_tc<6><<<tl.nchunks, TC_THREADS, TcLayout<6>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, C2, h->d_colidx, h->eta, h->etap,
-                    h->d_partial, h->d_cg_iters + 2);
-                break;
-            case 5:
-                k_hist_tc<5><<<tl.nchunks, TC_THREADS, TcLayout<5>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, C2, h->d_colidx, h->eta, h->etap,
-                    h->d_partial, h->d_cg_iters + 2);
-                break;
-            default:
-                k_hist_tc<4><<<tl.nchunks, TC_THREADS, TcLayout<4>::bytes(h->npad), s>>>(
-                    pt, tl.chunks, reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16), r16, w16, step_i, h->R, h->npad, C2, h->d_colidx, h->eta, h->etap,
-                    h->d_partial, h->d_cg_iters + 2);
+        const auto* t16 = reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16);
+#define MOT_TC_LAUNCH(NSV, BV)                                                                                      \
+    k_hist_tc<NSV, BV><<<tl.nchunks, TC_THREADS, TcLayout<NSV, BV>::bytes(h->npad), s>>>(                          \
+        pt, tl.chunks, t16, r16, w16, step_i, h->R, h->npad, C2, h->d_colidx, h->eta, h->etap, h->d_partial,        \
+        h->d_cg_iters + 2, stall, 1000000ull)
+        const int ns = history_tc_stages(h->npad, h->tc_bulk);
+        if (h->tc_bulk) {
+            if (ns == 5) MOT_TC_LAUNCH(5, true);
+            else MOT_TC_LAUNCH(4, true);
+        } else {
+            if (ns == 6) MOT_TC_LAUNCH(6, false);
+            else if (ns == 5) MOT_TC_LAUNCH(5, false);
+            else MOT_TC_LAUNCH(4, false);
         }
+#undef MOT_TC_LAUNCH
         if (timed) {
             cudaEventRecord(h->ev1, s);
             h->ev_pending = true;

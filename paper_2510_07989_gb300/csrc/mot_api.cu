@@ -393,13 +393,17 @@ int gmres(mot_handle* h, const Work& W, const double* b, double* x, bool have_x0
 
 // x solves Q_0 x = rhs by right-preconditioned GMRES: Q_0 M z = rhs, x = M z,
 // with M the FP32 copy of Q_0^{-1} (mixed path) or its FP64 form (FP64 path
-// with fp64_precond); rhs must not be W.r, W.pd or W.q1
+// with fp64_precond). z lives in a buffer that apply_q0 does not touch: W.pd
+// on the mixed path (dense Q_0), W.s1 on the FP64 path (its product-form Q_0
+// uses W.pd inside the left factor; the history sums in W.s1 are consumed
+// before the solve). rhs must not be W.r, W.q1 or that buffer.
 int prec_solve(mot_handle* h, const Work& W, const double* rhs, double* x, double tol, cudaStream_t s) {
+    double* z = mixed(h) ? W.pd : W.s1;
     h->prec_active = true;
-    int st = gmres(h, W, rhs, W.pd, false, tol, s);
+    int st = gmres(h, W, rhs, z, false, tol, s);
     h->prec_active = false;
     if (!mixed(h)) {
-        launch_gemm_rect(h, 2 * h->npad, 2 * h->npad, h->d_Minv64, W.pd, h->B, x, s);
+        launch_gemm_rect(h, 2 * h->npad, 2 * h->npad, h->d_Minv64, z, h->B, x, s);
     } else if (h->emu_Minv.a16) {
         launch_emu_gemm(h, h->emu_Minv, W.pd, h->B, x, s);
     } else {
@@ -423,7 +427,7 @@ int ensure_state(mot_handle* h, int B) {
         int major = 0;
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
         h->hist_tc = mflag(h, MOT_MIX_HIST32) && mflag(h, MOT_MIX_TC) && B % 8 == 0 && major == 10 &&
-                      history_tc_fits(h->npad) && h->hist_tc_list.packed;
+                      history_tc_fits(h->npad, h->tc_bulk) && h->hist_tc_list.packed;
         if (h->hist_tc && !h->d_tiles16) {  // operator data: kept until mot_destroy
             // ntiles + 1 tiles: the last one stays zero (the missing partner of a merged task)
             h->d_tiles16 =
@@ -433,8 +437,9 @@ int ensure_state(mot_handle* h, int B) {
             CK(cudaDeviceSynchronize());
         }
         if (h->hist_tc) {
-            h->d_ring16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)h->R * 6 * bv);
-            h->d_win16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)(h->max_tail_lag + 1) * 3 * bv);
+            h->d_ring16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)h->R * history_tc_ring_slot_elems(h));
+            h->d_win16 = (uint16_t*)dalloc(h, sizeof(uint16_t) * (size_t)(h->max_tail_lag + 1) *
+                                                  history_tc_ring_slot_elems(h) / 2);
             if (!h->d_ring16 || !h->d_win16) return fail(h, MOT_EOOM, "device allocation of the march state");
         } else {
             h->d_ring32 = (float*)dalloc(h, sizeof(float) * (size_t)h->R * 6 * bv);
@@ -538,30 +543,48 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-int do_step(mot_handle* h, cudaStream_t s) {
+// One MOT step in three phases (a full step runs all of them on one stream):
+//   STEP_INPUTS   right-hand side, windowed sums of the K~ tail, reduced-precision panels
+//   STEP_HISTORY  the history contraction into W.s1, W.s2
+//   STEP_SOLVE    combine, left factor, Q_0 solve, ring update, recovery
+// mot_run_many runs the history of several scatterers as one launch between
+// their STEP_INPUTS and STEP_SOLVE phases.
+enum { STEP_INPUTS = 1, STEP_HISTORY = 2, STEP_SOLVE = 4, STEP_ALL = 7 };
+
+int do_step(mot_handle* h, cudaStream_t s, int phases = STEP_ALL) {
     Work W = work_of(h);
     const long long i = h->step + 1;
     const int n = h->npad * 2 * h->B;
     const size_t bv = (size_t)n;
-    CK(cudaMemsetAsync(h->d_cg_iters, 0, 3 * sizeof(int), s));
 #define PEV(k) \
     if (h->pev[0]) cudaEventRecord(h->pev[k], s)
-    PEV(0);
-    launch_rhs(h, i, W.rho1, W.rho2, s);
-    PEV(1);
     const bool mx = mixed(h);
     const bool h32 = mx && mflag(h, MOT_MIX_HIST32);
-    if (i >= 2) {
-        launch_window_sums(h, i, s);
-        if (h->hist_tc) {
-            if (h->max_tail_lag >= 1) launch_split3(h, h->max_tail_lag + 1, h->d_win, h->d_win16, s);
-            launch_history_tc(h, h->hist_tc_list, i, W.s1, W.s2, s);
-        } else if (h32) {
-            if (h->max_tail_lag >= 1) launch_d2f(h, (size_t)(h->max_tail_lag + 1) * bv, h->d_win, h->d_win32, s);
-            launch_history32(h, h->hist, h->d_tiles32, h->d_ring32, h->d_win32, nullptr, 0, i, W.s1, W.s2, s);
-        } else {
-            launch_history(h, h->hist, h->d_tiles, h->d_ring, h->d_win, nullptr, 0, i, W.s1, W.s2, s);
+    if (phases & STEP_INPUTS) {
+        CK(cudaMemsetAsync(h->d_cg_iters, 0, 3 * sizeof(int), s));
+        PEV(0);
+        launch_rhs(h, i, W.rho1, W.rho2, s);
+        PEV(1);
+        if (i >= 2) {
+            launch_window_sums(h, i, s);
+            if (h->hist_tc) {
+                if (h->max_tail_lag >= 1) launch_split3(h, h->max_tail_lag + 1, h->d_win, h->d_win16, s);
+            } else if (h32) {
+                if (h->max_tail_lag >= 1)
+                    launch_d2f(h, (size_t)(h->max_tail_lag + 1) * bv, h->d_win, h->d_win32, s);
+            }
         }
+    }
+    if ((phases & STEP_HISTORY) && i >= 2) {
+        if (h->hist_tc)
+            launch_history_tc(h, h->hist_tc_list, i, W.s1, W.s2, s);
+        else if (h32)
+            launch_history32(h, h->hist, h->d_tiles32, h->d_ring32, h->d_win32, nullptr, 0, i, W.s1, W.s2, s);
+        else
+            launch_history(h, h->hist, h->d_tiles, h->d_ring, h->d_win, nullptr, 0, i, W.s1, W.s2, s);
+    }
+    if (!(phases & STEP_SOLVE)) return MOT_OK;
+    if (i >= 2) {
         launch_axpby(h, n, 1.0, W.rho1, -1.0, W.s1, W.y1, s);
         launch_axpby(h, n, 1.0, W.rho2, -1.0, W.s2, W.y2, s);
     } else {
@@ -697,6 +720,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
         h->opt.mixed_flags = opt->mixed_flags;
         h->opt.refine_sweeps = opt->refine_sweeps;
         h->opt.fp64_precond = opt->fp64_precond;
+        h->opt.hist_stall_test = opt->hist_stall_test;
     }
     auto bad = [&](const char* m) {
         h->err = m;
@@ -983,7 +1007,16 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
             mid[3 * p + d] = 0.5 * (h->verts[3 * h->ev[2 * e] + d] + h->verts[3 * h->ev[2 * e + 1] + d]);
     }
     std::vector<int> colidx((size_t)nrb * np, h->ne < np ? h->ne : 0), colpos((size_t)nrb * np, 0);
-    {
+    if (h->tc_bulk) {
+        // bulk form of the tensor-core history: one global column order (the
+        // Morton order of the rows), so that the coefficient panel of column
+        // block cb is the contiguous ring rows [32 cb, 32 cb + 32)
+        for (int rb = 0; rb < nrb; rb++)
+            for (int j = 0; j < np; j++) {
+                colidx[(size_t)rb * np + j] = j;
+                colpos[(size_t)rb * np + j] = j;
+            }
+    } else {
         auto sort_rb = [&](int t0, int nth) {
             std::vector<std::pair<double, int>> dist(h->ne);
             for (int rb = t0; rb < nrb; rb += nth) {
@@ -1408,6 +1441,7 @@ MOT_API int mot_load_operators(mot_handle* h, const mot_operators* ops) {
     if (!h->d_rhs_x || !h->d_rhs_wf) return fail(h, MOT_EOOM, "device allocation (RHS table)");
     CK(cudaMemcpy(h->d_rhs_x, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->d_rhs_wf, wf.data(), sizeof(double) * wf.size(), cudaMemcpyHostToDevice));
+    h->tc_bulk = h->opt.precision == MOT_PREC_MIXED && mflag(h, MOT_MIX_TC) && mflag(h, MOT_MIX_TCBULK);
     if ((st = build_tiles(h, ops)) != MOT_OK) return st;
     if (h->opt.precision == MOT_PREC_MIXED && (st = precompute_mixed(h)) != MOT_OK) return st;
     if (h->opt.precision == MOT_PREC_FP64 && h->opt.fp64_precond && (st = precompute_fp64_precond(h)) != MOT_OK)

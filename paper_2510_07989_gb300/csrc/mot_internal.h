@@ -162,7 +162,9 @@ struct mot_handle {
     float* d_ring32 = nullptr;     // FP32 copy of the coefficient ring
     float* d_win32 = nullptr;      // FP32 windowed sums
     uint16_t* d_ring16 = nullptr;  // tensor-core path: bf16 slices of l and s, [R][2 parts][3 slices][npad][2B]
+                                   // (bulk form: [npad x 128] per slice, in swizzled 32-row blocks)
     uint16_t* d_win16 = nullptr;   // tensor-core path: bf16 slices of the windowed sums, [a][3 slices][npad][2B]
+    bool tc_bulk = false;          // tensor-core history in the bulk form (global column order, blocked ring)
     bool hist_tc = false;          // history contraction on the tensor cores (mixed path, B a multiple of 8)
     double* d_Q0 = nullptr;        // dense Q_0, (2 npad)^2, interleaved (edge, component) order, FP64
     float* d_Q0f = nullptr;        // FP32 copy
@@ -235,7 +237,8 @@ void launch_split3(mot_handle* h, int npanels, const double* src, uint16_t* dst,
 void launch_split_tiles(mot_handle* h, cudaStream_t s);
 // bf16 slices of l and s of ring slot `slot` (from the FP64 ring's [-v, u] variant)
 void launch_split_ring(mot_handle* h, int slot, cudaStream_t s);
-bool history_tc_fits(int npad);  // the row block's column order fits in shared memory
+bool history_tc_fits(int npad, bool bulk);  // the kernel's shared memory fits (gathered form: with the column order)
+size_t history_tc_ring_slot_elems(const mot_handle* h);  // bf16 elements of one ring slot of d_ring16
 
 // emulated FP64 products on tensor cores (k_emu64.cu): Y (M x N) = A X with A
 // prepared once by emu_prepare from the device FP64 matrix A (M x K, ld K)

@@ -26,6 +26,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+// Raise the barrier's expected transaction count without arriving.
+__device__ __forceinline__ void mbar_add_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -39,15 +43,15 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Slow path of a bounded wait: gives up when the CTA's abort flag is set or
-// after WAIT_NS (then it raises the flag and records `code` in *err).
+// after `bound` ns (then it raises the flag and records `code` in *err).
 static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                            int code) {
+                                                   int code, unsigned long long bound) {
     const unsigned long long t0 = gtimer();
     for (;;) {
         for (int i = 0; i < 64; i++)
             if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (gtimer() - t0 > WAIT_NS) {
+        if (gtimer() - t0 > bound) {
             *abort_flag = 1;
             atomicExch(err, code);
             return false;
@@ -55,17 +59,18 @@ static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity
     }
 }
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
+                                          int code, unsigned long long bound = WAIT_NS) {
 #pragma unroll 1
     for (int i = 0; i < 4096; i++)
         if (mbar_try(bar, parity)) return true;
-    return mbar_wait_slow(bar, parity, abort_flag, err, code);
+    return mbar_wait_slow(bar, parity, abort_flag, err, code, bound);
 }
 // Wait used while shutting down: bounded, ignores the abort flag.
-static __device__ __noinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity) {
+static __device__ __noinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity,
+                                                    unsigned long long bound = WAIT_NS) {
     const unsigned long long t0 = gtimer();
     while (!mbar_try(bar, parity))
-        if (gtimer() - t0 > WAIT_NS) return;
+        if (gtimer() - t0 > bound) return;
 }
 
 __device__ __forceinline__ void fence_barrier_init() {
@@ -79,6 +84,19 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+
+// 16-byte global -> shared copy (cp.async, L2 only)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+// Arrive on the mbarrier once all prior cp.async copies of this thread have
+// landed (the arrival is counted in the barrier's expected count).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Orders this thread's generic-proxy shared-memory writes before later async-proxy reads.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }

@@ -194,6 +194,30 @@ def ellipsoid(freq: int, semi_axes, rotation: np.ndarray) -> Mesh:
     return build_edges(out)
 
 
+def uneven_batch(count: int = 24, seed: int = 20251007):
+    """The uneven batch of scatterers: icosphere levels 1, 2, 3 (radius 1)
+    and count - 3 ellipsoids, geodesic frequency-n spheres (20 n^2
+    triangles) with n drawn from {3, ..., 11}, semi-axes from U[0.5, 1.5]^3
+    and a random rotation; eps_r from U[1.5, 8] for every scatterer.
+    Scatterer s draws from numpy default_rng(seed + s). Returns a list of
+    (mesh, eps_r)."""
+    out = []
+    for s in range(count):
+        rng = np.random.default_rng(seed + s)
+        if s < 3:
+            mesh = icosphere(s + 1)
+        else:
+            n = int(rng.integers(3, 12))
+            axes = rng.uniform(0.5, 1.5, size=3)
+            q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+            q = q * np.sign(np.diag(r))[None, :]
+            if np.linalg.det(q) < 0:
+                q[:, 0] = -q[:, 0]
+            mesh = ellipsoid(n, axes, q)
+        out.append((mesh, float(rng.uniform(1.5, 8.0))))
+    return out
+
+
 def torus(R: float = 1.0, r: float = 0.3, nu: int = 64, nv: int = 24) -> Mesh:
     """Torus grid of nu (major) x nv (minor) vertices; every quad is split along
     the same diagonal (2 nu nv triangles)."""

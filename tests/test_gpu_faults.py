@@ -54,3 +54,31 @@ def test_cg_iteration_limit_flags_and_continues(M, pr1_ops):
     assert M.MOT_ENOCONV in codes and set(codes) <= {M.MOT_OK, M.MOT_ENOCONV}
     assert s.info()["step"] == n
     assert "CG" in M.mot_last_error(s.h)
+
+
+def test_history_wait_bound_ends_in_error_status(M):
+    """The device side of failure detection, in the allowed form: with
+    hist_stall_test the first CTA of every tensor-core history launch withholds
+    one stage's copies and arrivals (a barrier phase nothing completes) and its
+    waits give up after 1 ms. The CTA takes its abort path (stops issuing,
+    drains the copies in flight, releases TMEM, raises the error word) and
+    mot_step returns MOT_ECUDA; the context stays usable: a fresh handle then
+    marches to the oracle's result."""
+    from oracle import mot as O
+    from paper_2510_07989_gb300.inputs.assemble import assemble
+    ops = assemble(MS.torus(1.0, 0.3, 12, 6), 4.0, 1.0, 0.1)
+    exc = MS.fibonacci_batch(64, ops.dt, w_steps=30, t0_steps=60)
+    waves = M.mot_waves(exc)
+    s = M.Solver(ops, precision=M.MOT_PREC_MIXED, hist_stall_test=4)
+    with pytest.raises(M.MotError) as e:
+        for _ in range(ops.kmax + 8):
+            M.mot_step(s.h, waves, 64)
+    assert e.value.code == M.MOT_ECUDA and "ran out of time" in str(e.value)
+    assert M.mot_get_info(s.h)["hist_kernel"] == 2
+    del s
+    n = 100
+    s2 = M.Solver(ops, precision=M.MOT_PREC_MIXED)
+    W = s2.run(exc, n)
+    assert s2.noconv == 0
+    ref = O.march(O.build_system(ops), exc, n, b=5)
+    assert np.abs(W[:, 5].reshape(n, -1) - ref).max() < 1e-6 * np.abs(ref).max()

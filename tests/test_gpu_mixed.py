@@ -96,6 +96,42 @@ def test_tensor_core_history_matches_oracle(M, torus_small):
     assert max(errs[0], errs[2]) <= max(errs_cc)
 
 
+@pytest.mark.parametrize("B", [32, 16, 8])
+def test_tensor_core_history_smaller_batches(M, torus_small, B):
+    """A batch that is a multiple of 8 below 64 (the cube configuration's 32,
+    the uneven batch's 16) also runs the tensor-core history, filling the first
+    2B of the 128 MMA rows: the first and last waves against the FP64 oracle
+    over every step, on the torus 12 x 6 with its 53 lags."""
+    ops, S = torus_small
+    exc = MS.fibonacci_batch(B, ops.dt, w_steps=30, t0_steps=60)
+    n = 130
+    s = M.Solver(ops, precision=M.MOT_PREC_MIXED)
+    W = s.run(exc, n)
+    assert s.info()["hist_kernel"] == 2 and s.noconv == 0
+    errs = [rel(W[:, b].reshape(n, -1), O.march(S, exc, n, b=b)) for b in (0, B - 1)]
+    print(f"tensor-core history, torus 12x6 B={B} max rel errs", ["%.3e" % e for e in errs])
+    assert max(errs) < TOL_MIXED
+
+
+@pytest.mark.parametrize("B", [64, 32])
+def test_tensor_core_history_bulk_form(M, torus_small, B):
+    """The bulk form of the tensor-core history (one global column order,
+    pre-swizzled 32-row coefficient blocks moved by bulk copies): against the
+    FP64 oracle over every step on the torus 12 x 6 (53 lags, ragged last row
+    block), and against the gathered form on the same waves."""
+    ops, S = torus_small
+    exc = MS.fibonacci_batch(B, ops.dt, w_steps=30, t0_steps=60)
+    n = 130
+    s = M.Solver(ops, precision=M.MOT_PREC_MIXED, mixed_flags=M.MOT_MIX_DEFAULT | M.MOT_MIX_TCBULK)
+    W = s.run(exc, n)
+    assert s.info()["hist_kernel"] == 2 and s.noconv == 0
+    errs = [rel(W[:, b].reshape(n, -1), O.march(S, exc, n, b=b)) for b in (0, B // 2 + 1, B - 1)]
+    print(f"tensor-core history, bulk form, torus 12x6 B={B} max rel errs", ["%.3e" % e for e in errs])
+    assert max(errs) < TOL_MIXED
+    Wg = M.Solver(ops, precision=M.MOT_PREC_MIXED, mixed_flags=M.MOT_MIX_DEFAULT & ~M.MOT_MIX_TCBULK).run(exc, n)
+    assert np.abs(W - Wg).max() < TOL_MIXED * np.abs(Wg).max()
+
+
 def test_mixed_save_load_state_resumes_exactly(M, torus_small):
     """mot_save_state / mot_load_state on the mixed path (reduced-precision ring
     copies rebuilt from the FP64 ring): the resumed run repeats the original."""
@@ -115,8 +151,9 @@ def test_small_cube_regime(M):
     """The cube configuration's regime at a size the oracle marches in
     seconds: non-smooth cube (side 2, 6 cells per edge: 432 triangles, 648
     edges), eps_r = 6, c dt = 0.25 (k_max = 34, 35 history lags). FP64, one
-    wave, within 1e-10; mixed, 64 waves (tensor-core history), sampled waves
-    within 1e-6 -- both against the oracle over 160 steps (pulse inside)."""
+    wave, within 1e-10; mixed with the configuration's 32 waves (tensor-core
+    history), sampled waves within 1e-6 -- both against the oracle over 160
+    steps (pulse inside)."""
     import math
     ops = assemble(MS.cube(2.0, 6), 6.0, 1.0, 0.25)
     assert ops.kmax == 34
@@ -126,11 +163,11 @@ def test_small_cube_regime(M):
     one = MS.single_wave(0.25, 30, 60, r_obj=r)
     W1 = M.Solver(ops).run(one, n)[:, 0].reshape(n, -1)
     e64 = rel(W1, O.march(S, one, n))
-    batch = MS.fibonacci_batch(64, 0.25, w_steps=30, t0_steps=60, r_obj=r)
+    batch = MS.fibonacci_batch(32, 0.25, w_steps=30, t0_steps=60, r_obj=r)
     s = M.Solver(ops, precision=M.MOT_PREC_MIXED)
     W = s.run(batch, n)
     assert s.info()["hist_kernel"] == 2
-    errs = [rel(W[:, b].reshape(n, -1), O.march(S, batch, n, b=b)) for b in (0, 29, 63)]
-    print(f"cube 6/edge: FP64 rel err {e64:.3e}; mixed B=64 rel errs", ["%.3e" % e for e in errs])
+    errs = [rel(W[:, b].reshape(n, -1), O.march(S, batch, n, b=b)) for b in (0, 13, 31)]
+    print(f"cube 6/edge: FP64 rel err {e64:.3e}; mixed B=32 rel errs", ["%.3e" % e for e in errs])
     assert e64 < 1e-10
     assert max(errs) < TOL_MIXED
