@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="torus64x24", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="torus64x24", choices=sorted(WORKLOADS) + ["uneven24"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tc-form", default="default", choices=["default", "gathered", "bulk"],
@@ -269,7 +269,17 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    ops, exc, _ = make_workload(args.workload)
+    if args.workload == "uneven24":  # the oracle on the batch's largest scatterer
+        from paper_2510_07989_gb300.inputs import meshes as MS
+        from paper_2510_07989_gb300.inputs.assemble import assemble
+        specs = MS.uneven_batch(24)
+        i = max(range(len(specs)), key=lambda k: specs[k][0].ne)
+        mesh, eps = specs[i]
+        ops = assemble(mesh, eps, 1.0, UNEVEN_DT, nq=3, ntheta=3, nrad=3, far_plain=6)
+        exc = MS.fibonacci_batch(UNEVEN_B, UNEVEN_DT, seed=20251007 + i,
+                                 r_obj=float(np.linalg.norm(mesh.verts, axis=1).max()))
+    else:
+        ops, exc, _ = make_workload(args.workload)
     from oracle import product as P
     sysP = P.ProductSystem(ops)
     ne = ops.ne
@@ -338,6 +348,8 @@ def march_arm(M, torch, ops, exc, args, local, world, precision, steps, warmup, 
     for i in range(1, n_pre + 1):
         M.mot_step(s.h, waves, B, host_out.numpy() if keep_waves else None, stream)
         keep(i)
+        if i == K + 1 and precision == M.MOT_PREC_MIXED and M.mot_get_info(s.h)["hist_kernel"] == 2:
+            M.mot_tune([s.h], stream)  # the history kernel's configuration, chosen at full depth
 
     def barrier():
         if world > 1:
@@ -482,6 +494,10 @@ def run_ours(args):
                                      "FP64 CG projector)") if args.precision == "mixed" else "fp64 plain",
                        "history_prefill_steps": K + 1,
                        "tc_form": args.tc_form,
+                       "tuner": {"chunk_cap": info1["tc_chunk_cap"], "lag_frac": info1["tc_lag_frac"],
+                                 "stages": info1["tc_stages"], "tuned": bool(info1["tc_tuned"]),
+                                 "tuned_launch_ms": info1["tc_tune_ms"]},
+                       "history_launches_before_timed": info0["tc_launches"],
                        "pulse": "paper's Gaussian (w = 120 c dt), peak at the scatterer centre at the middle of "
                                 "the device-timed window (t0 = (K + 1 + warmup + 1.5 steps) dt; the host-buffer "
                                 "window precedes it)",
@@ -526,10 +542,165 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+UNEVEN_DT = 0.2   # c dt of the uneven batch
+UNEVEN_B = 16     # plane waves per scatterer
+
+
+def run_uneven(args):
+    """The uneven batch: 24 scatterers (icospheres L1-L3 and 21 seeded
+    ellipsoids of 540-7260 unknowns, eps_r in [1.5, 8]), c dt = 0.2, 16 plane
+    waves each, marched together by mot_run_many: one history launch for all
+    of them per step (tuned once at full depth), the rest of every step on a
+    stream per scatterer. Timing as for one scatterer (host-buffer window,
+    then the device-timed window with the pulse at its middle)."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    from paper_2510_07989_gb300 import mot as M
+    from paper_2510_07989_gb300.build import build
+    from paper_2510_07989_gb300.inputs import meshes as MS
+    from paper_2510_07989_gb300.inputs.assemble import assemble
+    if rank == 0:
+        build()
+    if world > 1:
+        torch.distributed.barrier()
+    M.load_library()
+    specs = MS.uneven_batch(24, seed=20251007 + 1000 * rank)
+    flags = M.MOT_MIX_DEFAULT
+    if args.tc_form == "bulk":
+        flags |= M.MOT_MIX_TCBULK
+    elif args.tc_form == "gathered":
+        flags &= ~M.MOT_MIX_TCBULK
+    solvers, ops_keep, t_asm, t_load, kmax = [], {}, 0.0, 0.0, 0
+    check = (0, max(range(len(specs)), key=lambda i: specs[i][0].ne))  # smallest and largest scatterer
+    for i, (mesh, eps) in enumerate(specs):
+        t = time.time()
+        ops = assemble(mesh, eps, 1.0, UNEVEN_DT, nq=3, ntheta=3, nrad=3, far_plain=6)
+        t_asm += time.time() - t
+        t = time.time()
+        sv = M.Solver(ops, device=local, timing=1, precision=M.MOT_PREC_MIXED, mixed_flags=flags)
+        t_load += time.time() - t
+        kmax = max(kmax, ops.kmax)
+        if i in check:
+            ops_keep[i] = ops
+        sv.ops = None  # host operators not kept
+        solvers.append(sv)
+        del ops
+    n = len(solvers)
+    K = kmax + 1
+    n_pre = K + 1 + args.warmup
+    excs = []
+    for i, (mesh, _) in enumerate(specs):
+        r_obj = float(np.linalg.norm(mesh.verts, axis=1).max())
+        excs.append(MS.fibonacci_batch(UNEVEN_B, UNEVEN_DT, seed=20251007 + 1000 * rank + i,
+                                       t0_steps=n_pre + 1.5 * args.steps, r_obj=r_obj))
+    waves = [M.mot_waves(e) for e in excs]
+    Bs = [UNEVEN_B] * n
+    hs = [s_.h for s_ in solvers]
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(local)
+    clocks.start()
+    keep_pre = {i: np.zeros((n_pre, UNEVEN_B, 2, solvers[i].ne)) for i in check}
+    M.mot_run_many(hs, n_pre, waves, Bs, [keep_pre.get(i) for i in range(n)], stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    outs = [torch.empty((args.steps, UNEVEN_B, 2, sv.ne), dtype=torch.float64).pin_memory() for sv in solvers]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    M.mot_run_many(hs, args.steps, waves, Bs, [o.numpy() for o in outs], stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    info0 = [M.mot_get_info(h) for h in hs]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.begin()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    M.mot_run_many(hs, args.steps, waves, Bs, None, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.end()
+    barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    info1 = [M.mot_get_info(h) for h in hs]
+    ms_max, e2e_max = reduce_max([ms, e2e_ms], world)
+    units = n * UNEVEN_B
+    value = throughput(world, units, args.steps, ms_max)
+    if rank != 0:
+        return
+    peaks, how = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    hl = info1[0]["hist_timed_launches"] - info0[0]["hist_timed_launches"]
+    hms = info1[0]["hist_timed_ms"] - info0[0]["hist_timed_ms"]
+    ms_l = hms / hl if hl else None
+    hbytes = sum(x["hist_bytes_per_step"] for x in info1)
+    achieved = hbytes / (ms_l / 1e3) / 1e9 if ms_l else None
+    roof = {"kernel": "k_hist_tc (one launch for the 24 scatterers)", "bound": "hbm", "achieved": achieved,
+            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm if achieved else None, "traffic": None,
+            "peak_source": f"measured copy bandwidth ({how})", "algorithmic_bytes_per_launch": hbytes,
+            "launches_timed": hl, "ms_per_launch": ms_l,
+            "share_of_step": ms_l / (ms_max / args.steps) if ms_l else None}
+    line = {"metric": METRIC, "value": value, "unit": "RHS·steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "uneven24", "scatterers": n, "unknowns": [2 * sv.ne for sv in solvers],
+                       "eps_r": [round(e, 3) for _, e in specs], "c_dt": UNEVEN_DT, "rhs_per_scatterer": UNEVEN_B,
+                       "history_lags_max": K, "tc_form": args.tc_form,
+                       "tuner": {"chunk_cap": info1[0]["tc_chunk_cap"], "lag_frac": info1[0]["tc_lag_frac"],
+                                 "stages": info1[0]["tc_stages"], "tuned": bool(info1[0]["tc_tuned"]),
+                                 "tuned_launch_ms": info1[0]["tc_tune_ms"]},
+                       "assembly_s": round(t_asm, 1), "load_s": round(t_load, 1),
+                       "gmres_iters_per_step": sum(b["gmres_iters_total"] - a["gmres_iters_total"]
+                                                   for a, b in zip(info0, info1)) / (n * args.steps),
+                       "l2": "inputs larger than L2 (history tiles read per step %.1f GB)" % (
+                           sum(x["tile_count"] for x in info1) * 6144 / 1e9),
+                       "parallelism": f"replicas{world}"},
+            "clocks": ck,
+            "e2e": {"value": throughput(world, units, args.steps, e2e_max), "unit": "RHS·steps/s",
+                    "h2d_bytes_per_step": 80 * units, "d2h_bytes_per_step": sum(8 * 2 * sv.ne * UNEVEN_B
+                                                                                 for sv in solvers)},
+            "gpu_launches": sum(b["gpu_launches"] - a["gpu_launches"] for a, b in zip(info0, info1)),
+            "roofline": roof,
+            "peaks": {"source": how, "hbm_gbs": peaks.get("hbm_gbs")}}
+    if world == 1 and not args.no_cpu_baseline:
+        acc = []
+        el_tot = 0.0
+        for i in check:
+            hist = {j + 1: keep_pre[i][j, 0].reshape(-1) for j in range(n_pre)}
+            hist.update({n_pre + 1 + j: outs[i].numpy()[j, 0].reshape(-1).copy() for j in range(args.steps)})
+            c = n_pre + args.steps
+            w_ref, el, _ = oracle_one_step(ops_keep[i], excs[i], 0, hist, c)
+            el_tot += el
+            peak = max(np.linalg.norm(w) for w in hist.values())
+            acc.append({"scatterer": i, "unknowns": 2 * solvers[i].ne, "step": c, "wave": 0,
+                        "rel_err_2norm": float(np.linalg.norm(hist[c] - w_ref) / np.linalg.norm(w_ref)),
+                        "rel_err_vs_run_peak": float(np.linalg.norm(hist[c] - w_ref) / peak)})
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        line["cpu_baseline"] = {"value": len(check) / el_tot, "unit": "RHS·steps/s", "cores": cores,
+                                "kind": "oracle", "sample": "one full-depth MOT step x 1 RHS of the smallest and "
+                                                            "of the largest scatterer (product-form FP64 oracle, "
+                                                            "from the GPU's own history; set-up excluded)"}
+        line["accuracy"] = acc
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "uneven24":
+        run_uneven(args)
     else:
         run_ours(args)
 

@@ -203,6 +203,18 @@ typedef struct {
     /* GMRES iterations of the Q_0 solves summed over every step since the
        march (re)started (the refinement's correction solves excluded) */
     int64_t gmres_iters_total;
+    /* tensor-core history: the configuration in use -- tasks per chunk, the
+       fraction of the L2 one lag range of the task list may fill, pipeline
+       depth (0: the deepest that fits) -- whether mot_tune (or mot_run_many)
+       chose it, and its launch time in that tuning (ms) */
+    int32_t tc_chunk_cap;
+    double tc_lag_frac;
+    int32_t tc_stages;
+    int32_t tc_tuned;
+    double tc_tune_ms;
+    /* launches of the tensor-core history kernel that served this handle so far
+       (steps, tuning trials, launches shared with other scatterers) */
+    int64_t tc_launches;
 } mot_info;
 
 /*
@@ -258,8 +270,16 @@ int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, double* w_
  * on a stream of its own driven by a host thread of its own: each stream
  * starts after the work already queued on `stream` and `stream` waits for all
  * of them before its later work, so the latency-bound solves of the small
- * scatterers overlap the kernels of the large ones. Each scatterer's results
- * are those of the single mot_run (the same kernels in the same order).
+ * scatterers overlap the kernels of the large ones. The scatterers on the
+ * tensor-core history (mixed precision, B a multiple of 8; up to 32, of the
+ * first one's kernel form) march in lock step: every step, their history
+ * contractions run as ONE launch of the history kernel over all of them (each
+ * CTA serving one chunk of one scatterer), the rest of each step on its own
+ * stream; that group is tuned once (mot_tune) at the first step that
+ * contracts every member's full history. A scatterer outside the group gives
+ * the results of the single mot_run (same kernels, same order); one inside it
+ * those of a single march with the same tuned configuration (the history sums
+ * of a chunking differ from another's by rounding).
  *   hs      : n distinct handles with operators loaded, on the device of
  *             `stream` (a cudaStream_t, or NULL for the default stream).
  *   waves   : n arrays, waves[i] holding B[i] plane waves (host).
@@ -274,6 +294,23 @@ int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, double* w_
  */
 int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* const* waves, const int* B,
                  double* const* w_out, void* stream);
+
+/*
+ * Autotuner of the tensor-core history contraction (the paper has no
+ * counterpart; it only picks how the work of Eq. (MOT)'s history sum is cut).
+ * For n handles marched together (n = 1: one handle alone; n <= 32), every
+ * candidate configuration -- tasks per chunk in {256, 512, 1024}, fraction of
+ * the L2 a lag range may fill in {0.2, 0.4, 0.8}, pipeline depth in {4, 5, 6}
+ * where it fits -- is applied and its launch (one for all n handles) timed
+ * three times with CUDA events on `stream` after one warm-up; the fastest
+ * (median) is kept by every handle and reported by mot_get_info. The trial
+ * launches read the current march state and change nothing a later step
+ * reads. Requires handles on the tensor-core history (mixed precision, B a
+ * multiple of 8) of one kernel form on one device that have taken a step
+ * (MOT_ESTATE otherwise). mot_run_many tunes its group by itself, once, at
+ * the first step that contracts every member's full history.
+ */
+int mot_tune(mot_handle* const* hs, int n, void* stream);
 
 /* Recovered currents of the last step, [B][4][ne]: j loop, j star, m loop,
  * m star (Eq. (dis_jm)), host or device memory. Ordered after the handle's

@@ -154,11 +154,12 @@ struct TcLayout {
     static constexpr int NBARS = 2 * NS + 2 * NB + 1;  // + one barrier for the final MMA drain
     static constexpr size_t BARS = (size_t)NS * STAGE;
     static constexpr size_t SLOT = BARS + ((8 * NBARS + 15) / 16) * 16;  // TMEM address, abort flag, issued count
-    static constexpr size_t DESC = SLOT + 16;                             // TC_CHUNK packed tasks (uint4)
-    static constexpr size_t COLS = DESC + 16 * TC_CHUNK;                  // column order of the row block (uint16)
-    // the gathered form stages the row block's column order; the bulk form has none
-    static size_t bytes(int npad) { return COLS + (BULK ? 0 : (((size_t)npad * 2 + 15) / 16) * 16) + 1024; }
-    static_assert(BARS % 1024 == 0 && SLOT % 16 == 0 && DESC % 16 == 0 && COLS % 16 == 0,
+    static constexpr size_t DESC = SLOT + 16;  // the chunk's packed tasks (uint4), cap of them
+    // then, in the gathered form, the column order of the row block (uint16)
+    static size_t bytes(int npad, int cap) {
+        return DESC + 16 * (size_t)cap + (BULK ? 0 : (((size_t)npad * 2 + 15) / 16) * 16) + 1024;
+    }
+    static_assert(BARS % 1024 == 0 && SLOT % 16 == 0 && DESC % 16 == 0,
                   "shared-memory regions must keep their alignment (uint4 task loads)");
 };
 
@@ -180,14 +181,45 @@ __host__ __device__ __forceinline__ uint32_t blk_elem(int r, int m) {
 // half, v in the second), and one thread moves a stage with bulk copies: per
 // slice one 8 KB copy (or two 4 KB copies with the halves exchanged for
 // [-v, u]) and the six 2 KB tile slices, all counted in bytes on FULL.
+// One launch serves one or several scatterers (jobs): the launch's CTAs are
+// the chunks of job 0, then those of job 1, ... (cend: one past a job's last
+// CTA). Every job brings its own task list, tiles, ring, output and error word.
+struct TcJob {
+    const uint4* tasks;
+    const HistChunk* chunks;
+    const __nv_bfloat16* tiles16;
+    const __nv_bfloat16* ring16;
+    const __nv_bfloat16* win16;
+    const int* colidx;
+    double* partial;
+    int* err;
+    long long step_i;
+    double eta, etap;
+    int R, npad, C2, cend;
+};
+struct TcJobs {
+    int njobs;
+    TcJob job[MOT_TC_MAX_JOBS];
+};
+
 template <int NS, bool BULK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_hist_tc(const uint4* __restrict__ tasks, const HistChunk* __restrict__ chunks,
-              const __nv_bfloat16* __restrict__ tiles16,
-              const __nv_bfloat16* __restrict__ ring16, const __nv_bfloat16* __restrict__ win16, long long step_i,
-              int R, int npad, int C2, const int* __restrict__ colidx, double eta, double etap,
-              double* __restrict__ partial, int* __restrict__ err, int stall_task, unsigned long long stall_bound) {
+    k_hist_tc(const __grid_constant__ TcJobs jobs, int cap, int stall_task, unsigned long long stall_bound) {
     using L = TcLayout<NS, BULK>;
+    int jb = 0;
+    while (jb + 1 < jobs.njobs && (int)blockIdx.x >= jobs.job[jb].cend) jb++;
+    const TcJob& J = jobs.job[jb];
+    const int cta = (int)blockIdx.x - (jb ? jobs.job[jb - 1].cend : 0);  // chunk of this job
+    const uint4* __restrict__ tasks = J.tasks;
+    const __nv_bfloat16* __restrict__ tiles16 = J.tiles16;
+    const __nv_bfloat16* __restrict__ ring16 = J.ring16;
+    const __nv_bfloat16* __restrict__ win16 = J.win16;
+    const int* __restrict__ colidx = J.colidx;
+    double* __restrict__ partial = J.partial;
+    int* __restrict__ err = J.err;
+    const long long step_i = J.step_i;
+    const int R = J.R, npad = J.npad, C2 = J.C2;
+    const double eta = J.eta, etap = J.etap;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // swizzled operand atoms need 1 KB alignment: the launch adds 1 KB of slack
     unsigned char* smem = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
@@ -197,7 +229,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     int* issued_slot = reinterpret_cast<int*>(tmem_slot + 2);  // tasks whose copies the gather warps issued
     uint4* sdesc = reinterpret_cast<uint4*>(smem + L::DESC);
-    uint16_t* scol = reinterpret_cast<uint16_t*>(smem + L::COLS);
+    uint16_t* scol = reinterpret_cast<uint16_t*>(smem + L::DESC + 16 * (size_t)cap);
     // FULL: the coefficient rows (one arrival per copying thread, when its
     // cp.async copies have landed) and the tile slices (bytes of the bulk
     // copies, added to the barrier's transaction count) of a stage
@@ -208,13 +240,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t DRAIN = bar0 + 8u * (2 * NS + 2 * NB);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const HistChunk ch = chunks[blockIdx.x];
+    const HistChunk ch = J.chunks[cta];
     // failure test (stall_task >= 0): the first CTA withholds the copies and
     // arrivals of its task stall_task, and every wait of that CTA gives up
     // after stall_bound ns, so the launch ends through the abort path
     const bool stall_cta = stall_task >= 0 && blockIdx.x == 0;
     const unsigned long long bound = stall_cta ? stall_bound : WAIT_NS;
-    const int ntask = ch.count;  // <= TC_CHUNK
+    const int ntask = ch.count;  // <= cap
 
     // the chunk's task list and the row block's column order, staged once
     for (int i = tid; i < ntask; i += TC_THREADS) sdesc[i] = tasks[ch.first + i];
@@ -472,7 +504,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (ok && g >= 0) drain(g, cur);
         if (ocol >= 0) {
-            double* p0 = partial + (size_t)blockIdx.x * 2 * T * C2 + ocol;
+            double* p0 = partial + (size_t)cta * 2 * T * C2 + ocol;
             double* p1 = p0 + (size_t)T * C2;
 #pragma unroll
             for (int n = 0; n < 32; n++) {
@@ -627,18 +659,23 @@ size_t history_tc_ring_slot_elems(const mot_handle* h) {
 }
 
 
-// pipeline depth: the deepest that fits (next to the row block's column order
-// in the gathered form)
-int history_tc_stages(int npad, bool bulk) {
+// pipeline depth: the deepest that fits with `cap` staged tasks (and the row
+// block's column order in the gathered form)
+int history_tc_stages(int npad, bool bulk, int cap) {
     if (npad > 65536) return 0;
-    if (bulk) return TcLayout<5, true>::bytes(npad) <= TC_SMEM_MAX ? 5 : 4;
-    if (TcLayout<6, false>::bytes(npad) <= TC_SMEM_MAX) return 6;
-    if (TcLayout<5, false>::bytes(npad) <= TC_SMEM_MAX) return 5;
-    if (TcLayout<4, false>::bytes(npad) <= TC_SMEM_MAX) return 4;
+    const size_t mx = TC_SMEM_MAX;
+    if (bulk) {
+        if (TcLayout<6, true>::bytes(npad, cap) <= mx) return 6;
+        if (TcLayout<5, true>::bytes(npad, cap) <= mx) return 5;
+        return TcLayout<4, true>::bytes(npad, cap) <= mx ? 4 : 0;
+    }
+    if (TcLayout<6, false>::bytes(npad, cap) <= mx) return 6;
+    if (TcLayout<5, false>::bytes(npad, cap) <= mx) return 5;
+    if (TcLayout<4, false>::bytes(npad, cap) <= mx) return 4;
     return 0;
 }
 
-bool history_tc_fits(int npad, bool bulk) { return history_tc_stages(npad, bulk) > 0; }
+bool history_tc_fits(int npad, bool bulk) { return history_tc_stages(npad, bulk, MOT_TC_CHUNK) > 0; }
 
 void launch_split3(mot_handle* h, int npanels, const double* src, uint16_t* dst, cudaStream_t s) {
     const size_t n = (size_t)h->npad * 2 * h->B;
@@ -649,48 +686,128 @@ void launch_split3(mot_handle* h, int npanels, const double* src, uint16_t* dst,
     h->launches++;
 }
 
+namespace {
+
+TcJob job_of(mot_handle* h, long long step_i) {
+    TcJob j;
+    j.tasks = h->hist_tc_list.packed;
+    j.chunks = h->hist_tc_list.chunks;
+    j.tiles16 = reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16);
+    j.ring16 = reinterpret_cast<const __nv_bfloat16*>(h->d_ring16);
+    j.win16 = reinterpret_cast<const __nv_bfloat16*>(h->d_win16);
+    j.colidx = h->d_colidx;
+    j.partial = h->d_partial;
+    j.err = h->d_cg_iters + 2;
+    j.step_i = step_i;
+    j.eta = h->eta;
+    j.etap = h->etap;
+    j.R = h->R;
+    j.npad = h->npad;
+    j.C2 = 2 * h->B;
+    j.cend = 0;
+    return j;
+}
+
+// One launch of the history kernel over jobs[0 .. njobs) (all of one form);
+// the pipeline depth is the handles' tuned one (all equal), else the deepest
+// that fits.
+void launch_jobs(mot_handle* h0, TcJobs& jobs, int nctas, int max_npad, int cap, cudaStream_t s) {
+    static std::atomic<unsigned long long> attr{0};
+    once_per_device(attr, h0->dev, [] {
+        cudaFuncSetAttribute(k_hist_tc<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+        cudaFuncSetAttribute(k_hist_tc<5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+        cudaFuncSetAttribute(k_hist_tc<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+        cudaFuncSetAttribute(k_hist_tc<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+        cudaFuncSetAttribute(k_hist_tc<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+        cudaFuncSetAttribute(k_hist_tc<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+    });
+    // failure test of the bounded waits (mot_options.hist_stall_test), off by default
+    const int stall = h0->opt.hist_stall_test > 0 ? h0->opt.hist_stall_test - 1 : -1;
+    const int deepest = mot::history_tc_stages(max_npad, h0->tc_bulk, cap);
+    const int ns = h0->tc_stages > 0 ? std::min(h0->tc_stages, deepest) : deepest;
+#define MOT_TC_LAUNCH(NSV, BV)                                                                              \
+    k_hist_tc<NSV, BV><<<nctas, TC_THREADS, TcLayout<NSV, BV>::bytes(max_npad, cap), s>>>(jobs, cap, stall, \
+                                                                                          1000000ull)
+    if (h0->tc_bulk) {
+        if (ns == 6) MOT_TC_LAUNCH(6, true);
+        else if (ns == 5) MOT_TC_LAUNCH(5, true);
+        else MOT_TC_LAUNCH(4, true);
+    } else {
+        if (ns == 6) MOT_TC_LAUNCH(6, false);
+        else if (ns == 5) MOT_TC_LAUNCH(5, false);
+        else MOT_TC_LAUNCH(4, false);
+    }
+#undef MOT_TC_LAUNCH
+    h0->launches++;
+}
+
+}  // namespace
+
 void launch_history_tc(mot_handle* h, const TaskList& tl, long long step_i, double* out_s1, double* out_s2,
                        cudaStream_t s) {
     const int C2 = 2 * h->B;
     if (tl.nchunks > 0) {
         const bool timed = h->opt.timing && h->ev0 && step_i > h->K;
         if (timed) cudaEventRecord(h->ev0, s);
-        static std::atomic<unsigned long long> attr{0};
-        once_per_device(attr, h->dev, [] {
-            cudaFuncSetAttribute(k_hist_tc<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-            cudaFuncSetAttribute(k_hist_tc<5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-            cudaFuncSetAttribute(k_hist_tc<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-            cudaFuncSetAttribute(k_hist_tc<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-            cudaFuncSetAttribute(k_hist_tc<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-        });
-        // failure test of the bounded waits (mot_options.hist_stall_test), off by default
-        const int stall = h->opt.hist_stall_test > 0 ? h->opt.hist_stall_test - 1 : -1;
-        const uint4* pt = tl.packed;
-        const auto* r16 = reinterpret_cast<const __nv_bfloat16*>(h->d_ring16);
-        const auto* w16 = reinterpret_cast<const __nv_bfloat16*>(h->d_win16);
-        const auto* t16 = reinterpret_cast<const __nv_bfloat16*>(h->d_tiles16);
-#define MOT_TC_LAUNCH(NSV, BV)                                                                                      \
-    k_hist_tc<NSV, BV><<<tl.nchunks, TC_THREADS, TcLayout<NSV, BV>::bytes(h->npad), s>>>(                          \
-        pt, tl.chunks, t16, r16, w16, step_i, h->R, h->npad, C2, h->d_colidx, h->eta, h->etap, h->d_partial,        \
-        h->d_cg_iters + 2, stall, 1000000ull)
-        const int ns = history_tc_stages(h->npad, h->tc_bulk);
-        if (h->tc_bulk) {
-            if (ns == 5) MOT_TC_LAUNCH(5, true);
-            else MOT_TC_LAUNCH(4, true);
-        } else {
-            if (ns == 6) MOT_TC_LAUNCH(6, false);
-            else if (ns == 5) MOT_TC_LAUNCH(5, false);
-            else MOT_TC_LAUNCH(4, false);
-        }
-#undef MOT_TC_LAUNCH
+        TcJobs jobs;
+        jobs.njobs = 1;
+        jobs.job[0] = job_of(h, step_i);
+        jobs.job[0].tasks = tl.packed;
+        jobs.job[0].chunks = tl.chunks;
+        jobs.job[0].cend = tl.nchunks;
+        launch_jobs(h, jobs, tl.nchunks, h->npad, tl.cap, s);
+        h->tc_launches++;
         if (timed) {
             cudaEventRecord(h->ev1, s);
             h->ev_pending = true;
         }
-        h->launches++;
     }
     k_hist_reduce_idx<<<h->nrb, 256, 0, s>>>(tl.rb_ptr, tl.rb_chunks, h->d_partial, C2, out_s1, out_s2);
     h->launches++;
+}
+
+// The history of n scatterers (all on the tensor-core path, one form) in one
+// launch of the history kernel: step i of handle k is hs[k]->step + 1; the
+// chunk sums of every handle are then reduced into s1[k], s2[k]. All on
+// stream s. Returns the launch's duration in ms when `timed` (events on s).
+float launch_history_tc_many(mot_handle* const* hs, int n, double* const* s1, double* const* s2, cudaStream_t s,
+                             bool timed) {
+    TcJobs jobs;
+    jobs.njobs = n;
+    int nctas = 0, max_npad = 0, cap = 1;
+    for (int k = 0; k < n; k++) {
+        mot_handle* h = hs[k];
+        jobs.job[k] = job_of(h, h->step + 1);
+        nctas += h->hist_tc_list.nchunks;
+        jobs.job[k].cend = nctas;
+        max_npad = std::max(max_npad, h->npad);
+        cap = std::max(cap, h->hist_tc_list.cap);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed && nctas > 0) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+    }
+    if (nctas > 0) {
+        launch_jobs(hs[0], jobs, nctas, max_npad, cap, s);
+        for (int k = 0; k < n; k++) hs[k]->tc_launches++;
+    }
+    if (e1) cudaEventRecord(e1, s);
+    for (int k = 0; k < n; k++) {
+        mot_handle* h = hs[k];
+        k_hist_reduce_idx<<<h->nrb, 256, 0, s>>>(h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_partial,
+                                                 2 * h->B, s1[k], s2[k]);
+        h->launches++;
+    }
+    float ms = 0.f;
+    if (e1) {
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    return ms;
 }
 
 }  // namespace mot

@@ -18,6 +18,8 @@
 #include <tuple>
 #include <numeric>
 #include <string>
+#include <condition_variable>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -91,6 +93,11 @@ using namespace mot;
     do {                                                             \
         cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);       \
+    } while (0)
+#define CK_H(hh, call)                                               \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(hh, e_, #call);      \
     } while (0)
 
 namespace {
@@ -911,14 +918,27 @@ const int kKindFamily[NTK] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3};  // 0 A, 1 Ah, 2 At
 // lag range first, so the CTAs that run at the same time work on the same few
 // lags. Within a piece: coefficient transform (variant; windowed sums
 // separately), lag, column block.
-int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::vector<int>& rbs) {
+// cap: most tasks per chunk; lag_frac: the fraction of the L2 that the ring
+// slots of one lag range may fill (sets the lags per range).
+int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::vector<int>& rbs, int cap,
+                 double lag_frac) {
     const int nrb = h->nrb;
     int l2 = 0;
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->dev);
     if (l2 <= 0) l2 = 64 << 20;
     // bf16 slices of l and s of one lag for B = 64: 2 parts x 3 slices x npad x 128 x 2 bytes
     const double lag_bytes = 2.0 * 3.0 * h->npad * 128.0 * 2.0;
-    const int kr = std::max(1, (int)(0.4 * l2 / lag_bytes));
+    const int kr = std::max(1, (int)(lag_frac * l2 / lag_bytes));
+    {  // a list made before (re-tuning) is replaced
+        TaskList& old = h->hist_tc_list;
+        void* ptrs[] = {old.packed, old.chunks, old.rb_ptr, old.rb_chunks};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        old.packed = nullptr;
+        old.chunks = nullptr;
+        old.rb_ptr = old.rb_chunks = nullptr;
+        old.ntasks = old.nchunks = old.cap = 0;
+    }
     auto xform = [](int code) { return (code & 3) == 2 ? 3 : (code >> 2) & 3; };
     const unsigned zt = (unsigned)h->ntiles;  // index of the zero tile
     struct Merged {
@@ -949,7 +969,8 @@ int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::v
         if (a.k != b.k) return a.k < b.k;
         return a.cb < b.cb;
     });
-    const int cap = MOT_TC_CHUNK;  // tasks per chunk (staged in the CTA's shared memory)
+    cap = std::max(1, std::min(cap, MOT_TC_CHUNK));  // tasks per chunk (staged in the CTA's shared memory)
+    int maxcount = 0;
     std::vector<HistChunk> chunks;
     std::vector<std::vector<int>> per_rb(nrb);
     size_t i = 0;
@@ -959,6 +980,7 @@ int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::v
         while (j < m.size() && m[j].rb == rb && (m[j].k - 1) / kr == r && (int)(j - i) < cap) j++;
         per_rb[rb].push_back((int)chunks.size());
         chunks.push_back(HistChunk{rb, (int)i, (int)(j - i)});
+        maxcount = std::max(maxcount, (int)(j - i));
         i = j;
     }
     std::vector<int> rptr(nrb + 1, 0), rch;
@@ -976,6 +998,9 @@ int make_tc_list(mot_handle* h, const std::vector<HistTask>& tasks, const std::v
     TaskList& tl = h->hist_tc_list;
     tl.ntasks = (int)m.size();
     tl.nchunks = (int)chunks.size();
+    tl.cap = std::max(1, maxcount);
+    h->tc_cap = cap;
+    h->tc_lag_frac = lag_frac;
     tl.packed = (uint4*)dalloc(h, sizeof(uint4) * std::max<size_t>(1, packed.size()));
     tl.chunks = (HistChunk*)dalloc(h, sizeof(HistChunk) * std::max<size_t>(1, chunks.size()));
     tl.rb_ptr = (int*)dalloc(h, sizeof(int) * (nrb + 1));
@@ -1220,9 +1245,11 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
     int st;
     if ((st = make_list(th_hist, rb_hist, h->hist)) != MOT_OK) return st;
     if ((st = make_list(th_lag0, rb_lag0, h->lag0)) != MOT_OK) return st;
-    if (h->opt.precision == MOT_PREC_MIXED && (h->opt.mixed_flags & MOT_MIX_TC) &&
-        (st = make_tc_list(h, th_hist, rb_hist)) != MOT_OK)
-        return st;
+    if (h->opt.precision == MOT_PREC_MIXED && (h->opt.mixed_flags & MOT_MIX_TC)) {
+        if ((st = make_tc_list(h, th_hist, rb_hist, MOT_TC_CHUNK, 0.4)) != MOT_OK) return st;
+        h->tc_tasks_host = std::move(th_hist);  // kept for re-chunking by the tuner
+        h->tc_rbs_host = std::move(rb_hist);
+    }
     h->d_tiles = (double*)dalloc(h, sizeof(double) * std::max<size_t>(1, tiles.size()));
     if (!h->d_tiles) return fail(h, MOT_EOOM, "device allocation (history tiles)");
     if (!tiles.empty()) CK(cudaMemcpy(h->d_tiles, tiles.data(), sizeof(double) * tiles.size(), cudaMemcpyHostToDevice));
@@ -1469,17 +1496,26 @@ MOT_API int mot_set_frequencies(mot_handle* h, int n_freq, const double* omega) 
     return MOT_OK;
 }
 
-MOT_API int mot_step(mot_handle* h, const mot_wave* waves, int B, double* w_out, void* stream) {
+namespace {
+
+// mot_step in two halves around its history contraction: step_begin checks
+// the call, uploads the waves and runs the STEP_INPUTS phase (with `phases`
+// = STEP_INPUTS | STEP_HISTORY also the history); step_end runs STEP_SOLVE
+// and returns w_i.
+int step_begin(mot_handle* h, const mot_wave* waves, int B, cudaStream_t s, int phases) {
     if (!h) return MOT_EINVAL;
     if (!h->loaded) return fail(h, MOT_ESTATE, "mot_load_operators must come first");
     if (B < 1 || B > MOT_MAX_B || !waves) return fail(h, MOT_EINVAL, "B must be in [1, 64] with B waves");
     int st;
     if ((st = check_waves(h, waves, B)) != MOT_OK) return st;
     CK(cudaSetDevice(h->dev));
-    cudaStream_t s = (cudaStream_t)stream;
     if ((st = ensure_state(h, B)) != MOT_OK) return st;
     if ((st = upload_waves(h, waves, B, s)) != MOT_OK) return st;
-    st = do_step(h, s);
+    return do_step(h, s, phases);
+}
+
+int step_end(mot_handle* h, int B, double* w_out, cudaStream_t s) {
+    int st = do_step(h, s, STEP_SOLVE);
     if (st != MOT_OK && st != MOT_ENOCONV) return st;
     CK(cudaEventRecord(h->ev_state, s));
     if (w_out) {
@@ -1494,6 +1530,15 @@ MOT_API int mot_step(mot_handle* h, const mot_wave* waves, int B, double* w_out,
         CK(cudaGetLastError());
     }
     return st;
+}
+
+}  // namespace
+
+MOT_API int mot_step(mot_handle* h, const mot_wave* waves, int B, double* w_out, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const int st = step_begin(h, waves, B, s, STEP_INPUTS | STEP_HISTORY);
+    if (st != MOT_OK) return st;
+    return step_end(h, B, w_out, s);
 }
 
 MOT_API int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, double* w_out, void* stream) {
@@ -1511,6 +1556,120 @@ MOT_API int mot_run(mot_handle* h, int n_steps, const mot_wave* waves, int B, do
     return worst;
 }
 
+namespace {
+
+// Reusable barrier of a fixed number of host threads.
+class HostBarrier {
+   public:
+    explicit HostBarrier(int n) : n_(n) {}
+    void wait() {
+        std::unique_lock<std::mutex> lk(m_);
+        const long gen = gen_;
+        if (++count_ == n_) {
+            count_ = 0;
+            gen_++;
+            cv_.notify_all();
+        } else {
+            cv_.wait(lk, [&] { return gen_ != gen; });
+        }
+    }
+
+   private:
+    std::mutex m_;
+    std::condition_variable cv_;
+    int n_, count_ = 0;
+    long gen_ = 0;
+};
+
+// Grows the chunk-sum buffer of h to the current tensor-core list.
+int fit_partial(mot_handle* h) {
+    const size_t need = sizeof(double) * (size_t)std::max(1, h->hist_tc_list.nchunks) * 2 * MOT_TILE * 2 * h->B;
+    if (need <= h->partial_bytes) return MOT_OK;
+    cudaFree(h->d_partial);
+    h->device_bytes -= (int64_t)h->partial_bytes;
+    h->d_partial = (double*)dalloc(h, need);
+    if (!h->d_partial) return fail(h, MOT_EOOM, "device allocation (history chunk sums)");
+    h->partial_bytes = need;
+    return MOT_OK;
+}
+
+// Autotuner of the tensor-core history for handles marched together (one
+// launch serves all of them): every candidate (tasks per chunk, lags per L2
+// range, pipeline depth) is applied, launched once to warm up and three times
+// timed with CUDA events on s; the fastest (median) is kept. The launches
+// read the current march state and write only the chunk sums and the history
+// sums of the work area, which every step recomputes before use.
+int tune_tc(mot_handle* const* hs, int n, cudaStream_t s) {
+    std::vector<double*> s1(n), s2(n);
+    int max_npad = 0;
+    for (int k = 0; k < n; k++) {
+        Work W = work_of(hs[k]);
+        s1[k] = W.s1;
+        s2[k] = W.s2;
+        max_npad = std::max(max_npad, hs[k]->npad);
+    }
+    const bool bulk = hs[0]->tc_bulk;
+    float best = 1e30f;
+    int bcap = MOT_TC_CHUNK, bns = 0;
+    double blf = 0.4;
+    const int caps[] = {256, 512, 1024};
+    const double fracs[] = {0.2, 0.4, 0.8};
+    for (int cap : caps)
+        for (double lf : fracs) {
+            int st;
+            for (int k = 0; k < n; k++) {
+                if ((st = make_tc_list(hs[k], hs[k]->tc_tasks_host, hs[k]->tc_rbs_host, cap, lf)) != MOT_OK) return st;
+                if (!hs[k]->hist_tc_list.packed) return fail(hs[k], MOT_EINVAL, "tensor-core list not available");
+                if ((st = fit_partial(hs[k])) != MOT_OK) return st;
+            }
+            int listcap = 1;
+            for (int k = 0; k < n; k++) listcap = std::max(listcap, hs[k]->hist_tc_list.cap);
+            for (int ns = 4; ns <= 6; ns++) {
+                if (ns > history_tc_stages(max_npad, bulk, listcap)) continue;
+                for (int k = 0; k < n; k++) hs[k]->tc_stages = ns;
+                launch_history_tc_many(hs, n, s1.data(), s2.data(), s, false);
+                float t[3];
+                for (int r = 0; r < 3; r++) t[r] = launch_history_tc_many(hs, n, s1.data(), s2.data(), s, true);
+                std::sort(t, t + 3);
+                if (cudaGetLastError() != cudaSuccess) return fail(hs[0], MOT_ECUDA, "mot_tune: trial launch failed");
+                if (t[1] < best) {
+                    best = t[1];
+                    bcap = cap;
+                    blf = lf;
+                    bns = ns;
+                }
+            }
+        }
+    for (int k = 0; k < n; k++) {
+        int st;
+        if ((st = make_tc_list(hs[k], hs[k]->tc_tasks_host, hs[k]->tc_rbs_host, bcap, blf)) != MOT_OK) return st;
+        if ((st = fit_partial(hs[k])) != MOT_OK) return st;
+        hs[k]->tc_stages = bns;
+        hs[k]->tc_tuned = true;
+        hs[k]->tc_tune_ms = best;
+    }
+    CK_H(hs[0], cudaStreamSynchronize(s));
+    return MOT_OK;
+}
+
+}  // namespace
+
+MOT_API int mot_tune(mot_handle* const* hs, int n, void* stream) {
+    if (n < 1 || n > MOT_TC_MAX_JOBS || !hs) return MOT_EINVAL;
+    std::vector<const mot_handle*> seen(hs, hs + n);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end() || !seen[0]) return MOT_EINVAL;
+    for (int k = 0; k < n; k++) {
+        mot_handle* h = hs[k];
+        if (!h->hist_tc || h->step < 1)
+            return fail(h, MOT_ESTATE, "mot_tune: needs handles on the tensor-core history that have taken a step");
+        if (h->tc_bulk != hs[0]->tc_bulk || h->dev != hs[0]->dev)
+            return fail(h, MOT_EINVAL, "mot_tune: handles of one kernel form on one device");
+    }
+    CK_H(hs[0], cudaSetDevice(hs[0]->dev));
+    return tune_tc(hs, n, (cudaStream_t)stream);
+}
+
 MOT_API int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* const* waves, const int* B,
                          double* const* w_out, void* stream) {
     if (n < 0 || n_steps < 0) return MOT_EINVAL;
@@ -1525,6 +1684,28 @@ MOT_API int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wa
     }
     cudaStream_t user = (cudaStream_t)stream;
     std::vector<int> st(n, MOT_OK);
+    // march state of every scatterer (it decides which run the tensor-core history)
+    for (int i = 0; i < n; i++) {
+        mot_handle* h = hs[i];
+        if (!h->loaded) return fail(h, MOT_ESTATE, "mot_load_operators must come first");
+        if (B[i] < 1 || B[i] > MOT_MAX_B) return fail(h, MOT_EINVAL, "B must be in [1, 64] with B waves");
+        if (cudaSetDevice(h->dev) != cudaSuccess) return fail(h, MOT_ECUDA, "cudaSetDevice");
+        int e = ensure_state(h, B[i]);
+        if (e != MOT_OK) return e;
+    }
+    // the group whose history contractions run as one launch per step: the
+    // scatterers on the tensor-core history in the first one's form and device
+    std::vector<int> group;
+    for (int i = 0; i < n; i++) {
+        mot_handle* h = hs[i];
+        if (h->hist_tc && (group.empty() || (h->tc_bulk == hs[group[0]]->tc_bulk && h->dev == hs[group[0]]->dev)) &&
+            (int)group.size() < MOT_TC_MAX_JOBS)
+            group.push_back(i);
+    }
+    if (group.size() < 2) group.clear();
+    std::vector<int> slot(n, -1);
+    for (size_t g = 0; g < group.size(); g++) slot[group[g]] = (int)g;
+    const int ng = (int)group.size();
     // fork: every scatterer's stream waits for the work queued on `stream`
     cudaEvent_t fork = nullptr;
     {
@@ -1537,21 +1718,98 @@ MOT_API int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wa
             return cuda_fail(h0, e, "mot_run_many: fork event");
         }
     }
-    std::vector<cudaEvent_t> joins(n, nullptr);
+    std::vector<cudaEvent_t> joins(n, nullptr), ev_in(ng, nullptr);
+    cudaEvent_t ev_hist = nullptr;
+    cudaStream_t gs = nullptr;  // stream of the group's history launches
+    if (ng > 0) {
+        cudaError_t e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(gs, fork, 0);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_hist, cudaEventDisableTiming);
+        for (int g = 0; g < ng && e == cudaSuccess; g++) e = cudaEventCreateWithFlags(&ev_in[g], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(hs[0], e, "mot_run_many: group set-up");
+    }
+    HostBarrier bar(std::max(1, ng));
+    std::vector<char> gfail(ng, 0);
+    int group_status = MOT_OK;
+    // the group's history of the coming step, by the first member's thread
+    auto group_history = [&]() {
+        std::vector<mot_handle*> hm;
+        std::vector<double*> s1, s2;
+        bool full = true;
+        for (int g = 0; g < ng; g++) {
+            mot_handle* h = hs[group[g]];
+            if (gfail[g] || h->step + 1 < 2) continue;
+            cudaStreamWaitEvent(gs, ev_in[g], 0);
+            Work W = work_of(h);
+            hm.push_back(h);
+            s1.push_back(W.s1);
+            s2.push_back(W.s2);
+            full = full && h->step + 1 > h->K;
+        }
+        if (!hm.empty()) {
+            // tuned once, at the first step that contracts every member's full history
+            bool tuned = true;
+            for (mot_handle* h : hm) tuned = tuned && h->tc_tuned;
+            if (full && !tuned && (int)hm.size() == ng) {
+                const int t = tune_tc(hm.data(), (int)hm.size(), gs);
+                if (t != MOT_OK) group_status = t;
+            }
+            const bool timed = full && hm[0]->opt.timing;
+            const float ms = launch_history_tc_many(hm.data(), (int)hm.size(), s1.data(), s2.data(), gs, timed);
+            if (timed)
+                for (mot_handle* h : hm) {
+                    h->timed_ms += ms;
+                    h->timed_launches++;
+                }
+        }
+        cudaEventRecord(ev_hist, gs);
+    };
     auto march = [&](int i) {
         mot_handle* h = hs[i];
         if (cudaSetDevice(h->dev) != cudaSuccess) {
             st[i] = fail(h, MOT_ECUDA, "cudaSetDevice");
-            return;
+            if (slot[i] < 0) return;
         }
         cudaStream_t s = nullptr;
         cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, fork, 0);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            st[i] = cuda_fail(h, e, "mot_run_many: stream set-up");
+        if (e != cudaSuccess && st[i] == MOT_OK) st[i] = cuda_fail(h, e, "mot_run_many: stream set-up");
+        const int g = slot[i];
+        if (g < 0) {
+            if (st[i] == MOT_OK) st[i] = mot_run(h, n_steps, waves[i], B[i], w_out ? w_out[i] : nullptr, s);
         } else {
-            st[i] = mot_run(h, n_steps, waves[i], B[i], w_out ? w_out[i] : nullptr, s);
+            // lock step with the group: inputs, one history launch for all, solve
+            bool ok = st[i] == MOT_OK;
+            int worst = MOT_OK;
+            double* out = w_out ? w_out[i] : nullptr;
+            for (int k = 0; k < n_steps; k++) {
+                if (ok) {
+                    const int a = step_begin(h, waves[i], B[i], s, STEP_INPUTS);
+                    if (a != MOT_OK || cudaEventRecord(ev_in[g], s) != cudaSuccess) {
+                        st[i] = a != MOT_OK ? a : fail(h, MOT_ECUDA, "mot_run_many: event");
+                        ok = false;
+                    }
+                }
+                gfail[g] = !ok;
+                bar.wait();
+                if (g == 0) group_history();
+                bar.wait();
+                if (ok) {
+                    cudaStreamWaitEvent(s, ev_hist, 0);
+                    double* dst = out ? out + (size_t)k * B[i] * 2 * h->ne : nullptr;
+                    const int r = step_end(h, B[i], dst, s);
+                    if (r == MOT_ENOCONV) {
+                        worst = MOT_ENOCONV;
+                    } else if (r != MOT_OK) {
+                        st[i] = r;
+                        ok = false;
+                    }
+                }
+            }
+            if (ok) st[i] = worst;
+        }
+        if (joins[i]) {
             e = cudaEventRecord(joins[i], s);  // the join point, recorded whatever the status
             if (e != cudaSuccess && st[i] == MOT_OK) st[i] = cuda_fail(h, e, "mot_run_many: join event");
         }
@@ -1569,7 +1827,14 @@ MOT_API int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wa
             cudaStreamWaitEvent(user, joins[i], 0);
             cudaEventDestroy(joins[i]);
         }
+    if (gs) {
+        cudaStreamSynchronize(gs);
+        cudaStreamDestroy(gs);
+        cudaEventDestroy(ev_hist);
+        for (auto ev : ev_in) cudaEventDestroy(ev);
+    }
     cudaEventDestroy(fork);
+    if (group_status != MOT_OK) return group_status;
     int worst = MOT_OK;
     for (int i = 0; i < n; i++) {
         if (st[i] != MOT_OK && st[i] != MOT_ENOCONV) return st[i];
@@ -1738,6 +2003,12 @@ MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
     info->hist_bytes_per_step = vb * h->hist_nnz_unique + vb * (double)h->K * 2.0 * 2.0 * h->ne * Bc;
     info->hist_tc_tasks = h->hist_tc_list.ntasks;
     info->gmres_iters_total = h->gmres_iters_total;
+    info->tc_chunk_cap = h->tc_cap;
+    info->tc_lag_frac = h->tc_lag_frac;
+    info->tc_stages = h->tc_stages;
+    info->tc_tuned = h->tc_tuned ? 1 : 0;
+    info->tc_tune_ms = h->tc_tune_ms;
+    info->tc_launches = h->tc_launches;
     info->hist_timed_launches = h->timed_launches;
     info->hist_timed_ms = h->timed_ms;
     for (int k = 0; k < 8; k++) info->phase_ms[k] = h->phase_ms[k];

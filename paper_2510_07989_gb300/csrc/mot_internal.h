@@ -16,6 +16,8 @@
 #define MOT_MAX_B 64
 // Tasks per CTA of the tensor-core history kernel (staged in shared memory).
 #define MOT_TC_CHUNK 1024
+// Scatterers one launch of the tensor-core history kernel serves at most.
+#define MOT_TC_MAX_JOBS 32
 // Size (doubles) of the fixed device array used by mot_fields_noalloc.
 #define MOT_NOALLOC_FIELD_DOUBLES 262144
 
@@ -70,6 +72,7 @@ struct TaskList {
     // tensor-core list: merged tasks, x = tile for s1, y = tile for s2 (the
     // zero tile if absent), z = cb | k << 16 | (part | variant << 2) << 26
     uint4* packed = nullptr;
+    int cap = 0;  // tensor-core list: most tasks in one chunk (staged in shared memory)
 };
 
 struct mot_handle {
@@ -165,6 +168,14 @@ struct mot_handle {
                                    // (bulk form: [npad x 128] per slice, in swizzled 32-row blocks)
     uint16_t* d_win16 = nullptr;   // tensor-core path: bf16 slices of the windowed sums, [a][3 slices][npad][2B]
     bool tc_bulk = false;          // tensor-core history in the bulk form (global column order, blocked ring)
+    int tc_stages = 0;             // pipeline depth of the tensor-core history (0: the deepest that fits)
+    int tc_cap = 0;                // tasks per chunk the tensor-core list was cut with
+    double tc_lag_frac = 0;        // fraction of L2 a lag range of the list may fill
+    bool tc_tuned = false;         // the three were chosen by mot_tune
+    float tc_tune_ms = 0;          // the chosen configuration's launch time in the tuning (ms)
+    int64_t tc_launches = 0;       // history-kernel launches that served this handle
+    std::vector<HistTask> tc_tasks_host;  // the tensor-core list's tasks (host), for re-chunking
+    std::vector<int> tc_rbs_host;
     bool hist_tc = false;          // history contraction on the tensor cores (mixed path, B a multiple of 8)
     double* d_Q0 = nullptr;        // dense Q_0, (2 npad)^2, interleaved (edge, component) order, FP64
     float* d_Q0f = nullptr;        // FP32 copy
@@ -239,6 +250,9 @@ void launch_split_tiles(mot_handle* h, cudaStream_t s);
 void launch_split_ring(mot_handle* h, int slot, cudaStream_t s);
 bool history_tc_fits(int npad, bool bulk);  // the kernel's shared memory fits (gathered form: with the column order)
 size_t history_tc_ring_slot_elems(const mot_handle* h);  // bf16 elements of one ring slot of d_ring16
+int history_tc_stages(int npad, bool bulk, int cap);
+float launch_history_tc_many(mot_handle* const* hs, int n, double* const* s1, double* const* s2, cudaStream_t s,
+                             bool timed);
 
 // emulated FP64 products on tensor cores (k_emu64.cu): Y (M x N) = A X with A
 // prepared once by emu_prepare from the device FP64 matrix A (M x K, ld K)

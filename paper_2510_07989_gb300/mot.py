@@ -67,7 +67,9 @@ class mot_info(ctypes.Structure):
                 ("hist_bytes_per_step", ctypes.c_double), ("hist_timed_launches", ctypes.c_int64),
                 ("hist_timed_ms", ctypes.c_double), ("phase_ms", ctypes.c_double * 8),
                 ("hist_kernel", ctypes.c_int32), ("hist_tc_tasks", ctypes.c_int64),
-                ("gmres_iters_total", ctypes.c_int64)]
+                ("gmres_iters_total", ctypes.c_int64), ("tc_chunk_cap", ctypes.c_int32),
+                ("tc_lag_frac", ctypes.c_double), ("tc_stages", ctypes.c_int32), ("tc_tuned", ctypes.c_int32),
+                ("tc_tune_ms", ctypes.c_double), ("tc_launches", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,7 +78,7 @@ class mot_info(ctypes.Structure):
 
 
 EXPORTED = ["mot_create", "mot_load_operators", "mot_set_frequencies", "mot_step", "mot_run", "mot_run_many",
-            "mot_get_currents",
+            "mot_tune", "mot_get_currents",
             "mot_fields", "mot_fields_noalloc", "mot_reset", "mot_save_state", "mot_load_state", "mot_get_info",
             "mot_get_edges", "mot_last_error", "mot_destroy"]
 
@@ -100,6 +102,7 @@ def load_library(path: str = LIB_PATH):
     lib.mot_step.argtypes = [vp, vp, i32, vp, vp]
     lib.mot_run.argtypes = [vp, i32, vp, i32, vp, vp]
     lib.mot_run_many.argtypes = [vp, i32, i32, vp, vp, vp, vp]
+    lib.mot_tune.argtypes = [vp, i32, vp]
     lib.mot_get_currents.argtypes = [vp, vp]
     lib.mot_fields.argtypes = [vp, vp, i32, vp, vp]
     lib.mot_fields_noalloc.argtypes = [vp, vp, i32, vp, vp]
@@ -265,6 +268,15 @@ def mot_run_many(handles, n_steps: int, waves_list, B_list, w_out_list=None, str
     msgs = [f"[{i}] {lib.mot_last_error(h.ptr).decode()}" for i, h in enumerate(handles)
             if lib.mot_last_error(h.ptr)]
     raise MotError(code, "; ".join(msgs))
+
+
+def mot_tune(handles, stream=None) -> None:
+    """mot_tune: pick, by timing, the tensor-core history configuration of
+    the handles marched together (one handle: alone)."""
+    n = len(handles)
+    lib = load_library()
+    hs = (ctypes.c_void_p * max(n, 1))(*[h.ptr for h in handles])
+    _check(handles[0].ptr if n else None, lib.mot_tune(hs, n, _stream(stream)))
 
 
 def mot_get_currents(h: Handle, out) -> None:
