@@ -498,6 +498,7 @@ def run_ours(args):
                                  "stages": info1["tc_stages"], "tuned": bool(info1["tc_tuned"]),
                                  "tuned_launch_ms": info1["tc_tune_ms"]},
                        "history_launches_before_timed": info0["tc_launches"],
+                       "launches_before_timed": info0["gpu_launches"],
                        "pulse": "paper's Gaussian (w = 120 c dt), peak at the scatterer centre at the middle of "
                                 "the device-timed window (t0 = (K + 1 + warmup + 1.5 steps) dt; the host-buffer "
                                 "window precedes it)",

@@ -202,7 +202,10 @@ __global__ void k_coldot_reduce(int nchunk, int C, const double* __restrict__ pa
 }
 // r[row][c] = f[row][c] - mean over the N rows of column c (one CTA per column):
 // the consistent part of a graph-Laplacian right-hand side (see pcg_dense_prec)
-__global__ void k_demean_cols(int N, int C, const double* __restrict__ f, double* __restrict__ r) {
+// It is also scaled by a power of two to O(1) (exact); unscale[c] receives
+// the inverse factor, which the solution is multiplied by at the end.
+__global__ void k_demean_cols(int N, int C, const double* __restrict__ f, double* __restrict__ r,
+                              double* __restrict__ unscale) {
     __shared__ double red[256];
     const int c = blockIdx.x;
     double s = 0.0;
@@ -214,7 +217,26 @@ __global__ void k_demean_cols(int N, int C, const double* __restrict__ f, double
         __syncthreads();
     }
     const double mean = red[0] / (double)N;
-    for (int row = threadIdx.x; row < N; row += blockDim.x) r[(size_t)row * C + c] = f[(size_t)row * C + c] - mean;
+    __syncthreads();
+    double m = 0.0;
+    for (int row = threadIdx.x; row < N; row += blockDim.x) m = fmax(m, fabs(f[(size_t)row * C + c] - mean));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    const int e = red[0] > 0.0 ? ilogb(red[0]) : 0;
+    const double sc = ldexp(1.0, -e);
+    for (int row = threadIdx.x; row < N; row += blockDim.x)
+        r[(size_t)row * C + c] = (f[(size_t)row * C + c] - mean) * sc;
+    if (threadIdx.x == 0) unscale[c] = ldexp(1.0, e);
+}
+// z[row][c] *= f[c]
+__global__ void k_scale_cols(int N, int C, const double* __restrict__ f, double* __restrict__ z) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)N * C;
+         e += (size_t)gridDim.x * blockDim.x)
+        z[e] *= f[e % C];
 }
 // x += a p ; r -= a q with a = num/den per column (0 if den <= 0 or the column is done)
 __global__ void k_pcg_xr(int N, int C, const double* __restrict__ num, const double* __restrict__ den,
@@ -280,6 +302,7 @@ int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const 
     double* rr = pq + C;
     double* ff = rr + C;
     int* done = (int*)(ff + C);
+    double* unscale = ff + 2 * C;  // after the C ints of done (room for C doubles)
     const int nch = (N + 63) / 64;
     auto coldot = [&](const double* X, const double* Y, double* out) {
         k_coldot<<<nch, 256, 0, s>>>(N, C, X, Y, red);
@@ -296,7 +319,7 @@ int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const 
     cudaMemsetAsync(r, 0, sizeof(double) * blk, s);  // padded rows must be zero (finite) for M
     // f sums to zero only up to rounding; its mean is an inconsistent part that
     // CG cannot reduce, sizeable when x lies almost entirely in the loop space
-    k_demean_cols<<<C, 256, 0, s>>>(N, C, f, r);
+    k_demean_cols<<<C, 256, 0, s>>>(N, C, f, r, unscale);
     h->launches++;
     coldot(r, r, ff);
     precond(r, zz);
@@ -332,6 +355,8 @@ int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const 
         cudaMemcpyAsync(rz, rzn, sizeof(double) * C, cudaMemcpyDeviceToDevice, s);
         h->launches++;
     }
+    k_scale_cols<<<g, 256, 0, s>>>(N, C, unscale, z);
+    h->launches++;
     return it;
 }
 

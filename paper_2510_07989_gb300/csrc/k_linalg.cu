@@ -113,6 +113,29 @@ __device__ __forceinline__ double col_reduce(double v, double* red, double* colv
     return r;
 }
 
+template <int CW>
+__device__ __forceinline__ double col_reduce_max(double v, double* red, double* colv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off >= CW; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (lane < CW) red[warp * CW + lane] = v;
+    __syncthreads();
+    if (threadIdx.x < CW) {
+        double m = 0.0;
+        const int nw = blockDim.x >> 5;
+        for (int w = 0; w < nw; w++) m = fmax(m, red[w * CW + threadIdx.x]);
+        colv[threadIdx.x] = m;
+    }
+    __syncthreads();
+    const double r = colv[lane % CW];
+    __syncthreads();
+    return r;
+}
+
+// 2^-e with 2^e the power of two at or below m (1 for m = 0): multiplying by
+// it (and later by its inverse) is exact and brings a column to O(1)
+__device__ __forceinline__ double pow2_scale(double m) { return m > 0.0 ? ldexp(1.0, -ilogb(m)) : 1.0; }
+
 template <int CW, bool NORMAL>
 __global__ void __launch_bounds__(1024) k_cg(int N, int C, CsrV A, CsrV A2, const double* __restrict__ f,
                                              double* __restrict__ z, double* __restrict__ r, double* __restrict__ p,
@@ -143,10 +166,17 @@ __global__ void __launch_bounds__(1024) k_cg(int N, int C, CsrV A, CsrV A2, cons
         mean = col_reduce<CW>(part, red, colv) / (double)N;
         part = 0.0;
     }
+    // the column is scaled by a power of two to O(1) (exact) and the solution
+    // scaled back at the end, so sums of squares neither underflow nor
+    // overflow whatever the scale of f (late in a march f decays without bound)
+    for (int row = row0; row < N; row += RS)
+        if (cv) part = fmax(part, fabs(f[(size_t)row * C + c] - mean));
+    const double sc = pow2_scale(col_reduce_max<CW>(part, red, colv));
+    part = 0.0;
     for (int row = row0; row < N; row += RS)
         if (cv) {
             const size_t ix = (size_t)row * C + c;
-            const double v = f[ix] - mean;
+            const double v = (f[ix] - mean) * sc;
             z[ix] = 0.0;
             r[ix] = v;
             p[ix] = v;
@@ -205,6 +235,9 @@ __global__ void __launch_bounds__(1024) k_cg(int N, int C, CsrV A, CsrV A2, cons
         __syncthreads();
         it++;
     }
+    const double usc = 1.0 / sc;  // exact: sc is a power of two
+    for (int row = row0; row < N; row += RS)
+        if (cv) z[(size_t)row * C + c] *= usc;
     if (threadIdx.x == 0) {
         atomicMax(it_max, it);
         if (it >= maxit) atomicAdd(noconv, 1);
@@ -447,6 +480,35 @@ __global__ void k_gm_scale(int npad, int B, const double* __restrict__ w, const 
         const int b = (i % C2) % B;
         const double d = nrm[b];
         v[i] = (active[b] && d > 0.0) ? w[i] / d : 0.0;
+    }
+}
+
+// Per wave b (the u and v columns b and B + b of a block vector): sc[b] =
+// 2^-e, 2^e the power of two at or below max |x| over both columns (1 when
+// x is zero). One CTA per wave.
+__global__ void k_wave_scale(int npad, int B, const double* __restrict__ x, double* __restrict__ sc) {
+    __shared__ double red[256];
+    const int b = blockIdx.x, C2 = 2 * B;
+    double m = 0.0;
+    for (int i = threadIdx.x; i < 2 * npad; i += blockDim.x) {
+        const int row = i >> 1, col = (i & 1) ? B + b : b;
+        m = fmax(m, fabs(x[(size_t)row * C2 + col]));
+    }
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sc[b] = red[0] > 0.0 ? ldexp(1.0, -ilogb(red[0])) : 1.0;
+}
+
+// x[:, b] and x[:, B + b] times sc[b] (inverse: divided by it; exact, powers of two)
+__global__ void k_wave_apply(int npad, int B, const double* __restrict__ sc, int inverse, double* __restrict__ x) {
+    const int C2 = 2 * B;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad * C2; i += gridDim.x * blockDim.x) {
+        const double f = sc[(i % C2) % B];
+        x[i] = inverse ? x[i] / f : x[i] * f;
     }
 }
 
@@ -787,6 +849,17 @@ void launch_gm_update(mot_handle* h, const double* V, int nvec, const double* co
 void launch_gm_scale(mot_handle* h, const double* w, const double* nrm, double* v, cudaStream_t s) {
     const long long n = (long long)h->npad * 2 * h->B;
     k_gm_scale<<<grid_for(n), 256, 0, s>>>(h->npad, h->B, w, nrm, h->d_gm_active, v);
+    h->launches++;
+}
+
+void launch_wave_scale(mot_handle* h, const double* x, double* sc, cudaStream_t s) {
+    k_wave_scale<<<h->B, 256, 0, s>>>(h->npad, h->B, x, sc);
+    h->launches++;
+}
+
+void launch_wave_apply(mot_handle* h, const double* sc, bool inverse, double* x, cudaStream_t s) {
+    const long long n = (long long)h->npad * 2 * h->B;
+    k_wave_apply<<<grid_for(n), 256, 0, s>>>(h->npad, h->B, sc, inverse ? 1 : 0, x);
     h->launches++;
 }
 

@@ -484,9 +484,10 @@ int ensure_state(mot_handle* h, int B) {
     h->d_gm_active = (int*)dalloc(h, sizeof(int) * B);
     h->d_gm_jend = (int*)dalloc(h, sizeof(int) * B);
     h->d_gm_bnorm = (double*)dalloc(h, sizeof(double) * B);
+    h->d_wscale = (double*)dalloc(h, sizeof(double) * B);
     if (!h->d_waves || !h->d_ring || !h->d_win || !h->d_cur || !h->d_dft || !h->d_work || !h->d_partial ||
         !h->d_V || !h->d_H || !h->d_g || !h->d_cs || !h->d_sn || !h->d_red || !h->d_resid || !h->d_gm_active ||
-        !h->d_gm_jend || !h->d_gm_bnorm)
+        !h->d_gm_jend || !h->d_gm_bnorm || !h->d_wscale)
         return fail(h, MOT_EOOM, "device allocation of the march state");
     h->h_waves.assign(10 * B, NAN);
     return MOT_OK;
@@ -495,6 +496,7 @@ int ensure_state(mot_handle* h, int B) {
 void free_state(mot_handle* h) {
     void* ptrs[] = {h->d_waves, h->d_ring, h->d_win, h->d_cur, h->d_dft, h->d_work, h->d_partial, h->d_V, h->d_H,
                     h->d_g, h->d_cs, h->d_sn, h->d_red, h->d_resid, h->d_gm_active, h->d_gm_jend, h->d_gm_bnorm,
+                    h->d_wscale,
                     h->d_wprev1, h->d_wprev2};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -511,6 +513,7 @@ void free_state(mot_handle* h) {
     h->d_V = h->d_H = h->d_g = h->d_cs = h->d_sn = h->d_red = h->d_resid = nullptr;
     h->d_gm_active = h->d_gm_jend = nullptr;
     h->d_gm_bnorm = nullptr;
+    h->d_wscale = nullptr;
     h->B = 0;
     h->step = 0;
     h->gmres_iters_total = 0;
@@ -620,6 +623,14 @@ int do_step(mot_handle* h, cudaStream_t s, int phases = STEP_ALL) {
         launch_axpby(h, n, 2.0, h->d_wprev1, -1.0, h->d_wprev2, W.x, s);
     else if (i == 2)
         launch_axpby(h, n, 1.0, h->d_wprev1, 0.0, nullptr, W.x, s);
+    // every wave's system is solved at O(1) magnitude: b and the initial
+    // guess scaled by a power of two (exact), the solution scaled back. Late
+    // in a march the solution decays without bound; unscaled, the sums of
+    // squares of the solve (and the FP32 copies of the mixed path) would
+    // underflow long before the values themselves do.
+    launch_wave_scale(h, W.b, h->d_wscale, s);
+    launch_wave_apply(h, h->d_wscale, false, W.b, s);
+    if (have_x0) launch_wave_apply(h, h->d_wscale, false, W.x, s);
     const bool refine = mx && mflag(h, MOT_MIX_REFINE);
     const bool prec = (mx && h->d_Minvf) || (!mx && h->d_Minv64);
     // with refinement the reduced-precision solves only need 1e-6: each sweep gains ~6 digits
@@ -656,6 +667,7 @@ int do_step(mot_handle* h, cudaStream_t s, int phases = STEP_ALL) {
         }
         h->last_gmres_iters = gm_iters;
     }
+    launch_wave_apply(h, h->d_wscale, true, W.x, s);
     PEV(5);
     h->gmres_iters_total += h->last_gmres_iters;
     std::swap(h->d_wprev1, h->d_wprev2);

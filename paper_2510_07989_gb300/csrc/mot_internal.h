@@ -146,6 +146,7 @@ struct mot_handle {
     int* d_gm_active = nullptr;    // [B] GMRES system still iterating
     int* d_gm_jend = nullptr;      // [B] Krylov dimension reached
     double* d_gm_bnorm = nullptr;  // [B] |b|
+    double* d_wscale = nullptr;    // [B] power-of-two scale of each wave's Q_0 system in the step
     int* d_cg_iters = nullptr;     // [0] max CG iterations, [1] non-converged solves,
                                    // [2] tensor-core history: code of a wait that ran out (0 = none)
     int* h_cg_iters = nullptr;     // pinned
@@ -287,6 +288,9 @@ void launch_gm_norm(mot_handle* h, const double* w, double* out, cudaStream_t s)
 void launch_gm_scale(mot_handle* h, const double* w, const double* nrm, double* v, cudaStream_t s);
 void launch_gm_arnoldi_finish(mot_handle* h, int j, const double* hcol, const double* nrm, cudaStream_t s);
 void launch_gm_init(mot_handle* h, const double* beta, int first_cycle, cudaStream_t s);
+// power-of-two scale of every wave's system (sc[b] = 2^-e) and its application
+void launch_wave_scale(mot_handle* h, const double* x, double* sc, cudaStream_t s);
+void launch_wave_apply(mot_handle* h, const double* sc, bool inverse, double* x, cudaStream_t s);
 void launch_gm_solve_update(mot_handle* h, double* y, double* x, cudaStream_t s);
 
 }  // namespace mot

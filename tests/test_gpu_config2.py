@@ -5,8 +5,8 @@ t0 = 240 dt).
 
 * Parity at c dt = 0.05 (k_max = 57, 58 history lags) and c dt = 0.5
   (k_max = 6): the FP64 GPU march against the product-form FP64 oracle, one
-  step computed by the oracle from the GPU's own previous steps at steps 200,
-  300 and 400 (the window around the pulse), within 1e-10 of the run's peak
+  step computed by the oracle from the GPU's own previous steps at steps 200
+  and 300 (and 400 at c dt = 0.5), around the pulse, within 1e-10 of the run's peak
   step norm (the metric of the readings; at c dt = 0.5 the solution at step
   400 has decayed to ~1e-12 of that peak).
 * Late-time stability (Section VI-A): 10^4 steps at c dt = 0.5; the solution
@@ -29,6 +29,16 @@ def M():
     return mot
 
 
+_OPS = {}
+
+
+def l3_ops(cdt):
+    """The icosphere L3 operators at c dt, assembled once per module."""
+    if cdt not in _OPS:
+        _OPS[cdt] = assemble(MS.icosphere(3), 2.0, 1.0, cdt)
+    return _OPS[cdt]
+
+
 def oracle_step(sysP, exc, b, i, history):
     """w_i of wave b by the product-form oracle from history[j] = w_j, j < i."""
     ne = sysP.ne
@@ -42,12 +52,14 @@ def oracle_step(sysP, exc, b, i, history):
 
 @pytest.mark.parametrize("cdt", [0.05, 0.5])
 def test_icosphere_l3_fp64_parity(M, cdt):
-    ops = assemble(MS.icosphere(3), 2.0, 1.0, cdt)
+    """At c dt = 0.05 the FP64 path with the FP64 dense Q_0^{-1} preconditioner,
+    at c dt = 0.5 the plain (unpreconditioned) FP64 path."""
+    ops = l3_ops(cdt)
     assert ops.ne == 1920 and ops.kmax == {0.05: 57, 0.5: 6}[cdt]
     exc = MS.single_wave(cdt)
     K = ops.kmax + 1
-    checks = (200, 300, 400)
-    s = M.Solver(ops)
+    checks = (200, 300) if cdt == 0.05 else (200, 300, 400)
+    s = M.Solver(ops, fp64_precond=1 if cdt == 0.05 else 0)
     waves = M.mot_waves(exc)
     out = np.zeros((1, 2, ops.ne))
     hist = {}
@@ -68,7 +80,7 @@ def test_icosphere_l3_fp64_parity(M, cdt):
 
 
 def test_icosphere_l3_late_time_stability(M):
-    ops = assemble(MS.icosphere(3), 2.0, 1.0, 0.5)
+    ops = l3_ops(0.5)
     exc = MS.single_wave(0.5)
     n = 10000
     s = M.Solver(ops, fp64_precond=1)
@@ -77,11 +89,16 @@ def test_icosphere_l3_late_time_stability(M):
     norms = np.zeros(n)
     for i in range(n):
         M.mot_step(s.h, waves, 1, out)
-        norms[i] = np.linalg.norm(out)
+        norms[i] = np.abs(out).max()  # the largest coefficient: no sum of squares to underflow late
     assert s.noconv == 0
     peak = norms.max()
-    print(f"icosphere L3 c dt = 0.5, 10^4 steps: peak at step {norms.argmax() + 1}, "
-          f"|w| / peak at steps 1000, 5000, 10000: {norms[999] / peak:.2e}, {norms[4999] / peak:.2e}, "
-          f"{norms[-1] / peak:.2e}")
+    marks = (250, 500, 1000, 2000, 4000, 6000, 8000, 10000)
+    print(f"icosphere L3 c dt = 0.5, 10^4 steps: peak at step {norms.argmax() + 1}; |w| / peak at steps "
+          + ", ".join(f"{k}: {norms[k - 1] / peak:.2e}" for k in marks))
+    # the pulse's response is the peak; after it the norm decays (the solution
+    # keeps decaying geometrically, far below any precision floor: every
+    # solve works at O(1) magnitude) and never grows back
+    assert norms.argmax() < 1000
     assert norms[-1] < 1e-12 * peak
-    assert norms[-1000:].max() <= norms[-2000:-1000].max() + 1e-30 * peak
+    blocks = norms[1000:].reshape(-1, 1000).max(axis=1)
+    assert np.all(blocks[1:] <= blocks[:-1])
