@@ -215,6 +215,9 @@ typedef struct {
     /* launches of the tensor-core history kernel that served this handle so far
        (steps, tuning trials, launches shared with other scatterers) */
     int64_t tc_launches;
+    /* epilogue warps of the tensor-core history (4, or 8: two per TMEM lane
+       quarter, one output each); a tuning choice like the three above */
+    int32_t tc_epilogue_warps;
 } mot_info;
 
 /*
@@ -301,7 +304,8 @@ int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* cons
  * For n handles marched together (n = 1: one handle alone; n <= 32), every
  * candidate configuration -- tasks per chunk in {256, 512, 1024}, fraction of
  * the L2 a lag range may fill in {0.2, 0.4, 0.8}, pipeline depth in {4, 5, 6}
- * where it fits -- is applied and its launch (one for all n handles) timed
+ * where it fits, epilogue warps in {4, 8} -- is applied and its launch (one
+ * for all n handles) timed
  * three times with CUDA events on `stream` after one warm-up; the fastest
  * (median) is kept by every handle and reported by mot_get_info. The trial
  * launches read the current march state and change nothing a later step

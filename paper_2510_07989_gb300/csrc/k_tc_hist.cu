@@ -85,8 +85,12 @@ constexpr int B_SLICE = T * T * 2;          // 2048 bytes: one bf16 slice of a t
 constexpr int STAGE_A = 3 * A_SLICE;        // 24576
 constexpr int STAGE_B = 6 * B_SLICE;        // 12288: both tiles' slices, ordered X0 hi, X1 hi, X0 mid, X1 mid, X0 lo, X1 lo
 constexpr int STAGE = STAGE_A + STAGE_B;    // 36864
-constexpr int NPROD = 64, NEPI = 128;
-constexpr int TC_THREADS = NPROD + 32 + NEPI;  // 224: warps 0-1 gather, 2 MMA, 3-6 epilogue
+constexpr int NPROD = 64;
+// threads of a CTA with EW epilogue warps: warps 0-1 gather, 2 MMA, 3 .. 2 + EW
+// epilogue (EW = 4: each warp folds both outputs of its TMEM lane quarter;
+// EW = 8: two warps per quarter, one output each)
+template <int EW>
+__host__ __device__ constexpr int tc_threads() { return NPROD + 32 + 32 * EW; }
 constexpr int TC_CHUNK = MOT_TC_CHUNK;      // tasks per CTA (staged in shared memory)
 constexpr size_t TC_SMEM_MAX = 227 * 1024;
 
@@ -202,9 +206,10 @@ struct TcJobs {
     TcJob job[MOT_TC_MAX_JOBS];
 };
 
-template <int NS, bool BULK>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int NS, bool BULK, int EW>
+__global__ void __launch_bounds__(tc_threads<EW>(), 1)
     k_hist_tc(const __grid_constant__ TcJobs jobs, int cap, int stall_task, unsigned long long stall_bound) {
+    constexpr int TC_THREADS = tc_threads<EW>();
     using L = TcLayout<NS, BULK>;
     int jb = 0;
     while (jb + 1 < jobs.njobs && (int)blockIdx.x >= jobs.job[jb].cend) jb++;
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int b = 0; b < NB; b++) {
             mbar_init(ACCF(b), 1);
-            mbar_init(ACCE(b), NEPI / 32);
+            mbar_init(ACCE(b), EW);
         }
         mbar_init(DRAIN, 1);
         *abort_flag = 0;
@@ -445,9 +450,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int quarter = warp & 3;  // TMEM lanes [32 quarter, 32 quarter + 32)
         const int m = quarter * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-        float hs0[32], hc0[32], hs1[32], hc1[32];  // compensated sums of s1 and s2
+        // outputs this warp folds: both (EW = 4), or one (EW = 8: warps 3-6 s1, 7-10 s2)
+        constexpr int NO = EW == 8 ? 1 : 2;
+        const int o0 = EW == 8 ? (warp - 3) >> 2 : 0;
+        float hs[NO][32], hc[NO][32];  // compensated sums
 #pragma unroll
-        for (int n = 0; n < 32; n++) hs0[n] = hc0[n] = hs1[n] = hc1[n] = 0.f;
+        for (int o = 0; o < NO; o++)
+#pragma unroll
+            for (int n = 0; n < 32; n++) hs[o][n] = hc[o][n] = 0.f;
         // per-column scale of each coefficient transform. Gathered form: panel
         // column m is u of wave m (m < B) or v of wave m - B. Bulk form: u of
         // wave m & 63 in the first half (m < 64), v in the second.
@@ -456,14 +466,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int ocol = BULK ? ((m & 63) < Bw ? (m >> 6) * Bw + (m & 63) : -1) : (m < C2 ? m : -1);
         const float xs0 = ucol ? (float)eta : (float)(1.0 / eta), xs1 = ucol ? (float)etap : (float)(1.0 / etap),
                     xs2 = ucol ? -1.f : 1.f;
-        // folds buffer b (transform key) into the sums of output o
-        auto fold = [&](uint32_t col, float c, float (&hs)[32], float (&hc)[32], bool release, int b) {
+        // folds the 32 columns at col into sums o; the last fold of a buffer
+        // releases it (one arrival per epilogue warp)
+        auto fold = [&](uint32_t col, float c, int o, bool release, int b) {
             float va[32], vb[32];
             tmem_ld32(col + 64, va);   // terms of relative size 2^-8
             tmem_ld32(col + 128, vb);  // and 2^-16
             tmem_wait_ld();
 #pragma unroll
-            for (int n = 0; n < 32; n++) hc[n] += c * (va[n] + vb[n]);
+            for (int n = 0; n < 32; n++) hc[o][n] += c * (va[n] + vb[n]);
             tmem_ld32(col, va);  // the leading products
             tmem_wait_ld();
             if (release) {
@@ -472,7 +483,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (lane == 0) mbar_arrive(ACCE(b));
             }
 #pragma unroll
-            for (int n = 0; n < 32; n++) two_sum(hs[n], hc[n], c * va[n]);
+            for (int n = 0; n < 32; n++) two_sum(hs[o][n], hc[o][n], c * va[n]);
         };
         auto drain = [&](int gg, int key) -> bool {
             const int b = gg % NB;
@@ -481,8 +492,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __syncwarp();
             const float c = key == 0 ? xs0 : key == 1 ? xs1 : key == 2 ? xs2 : 1.f;
             const uint32_t col = tl + (uint32_t)(b * BUFCOLS);
-            fold(col, c, hs0, hc0, false, b);
-            fold(col + 32, c, hs1, hc1, true, b);
+#pragma unroll
+            for (int o = 0; o < NO; o++) fold(col + 32 * (o0 + o), c, o, o == NO - 1, b);
             return true;
         };
         int g = -1, ing = 0, cur = -1;
@@ -504,12 +515,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         if (ok && g >= 0) drain(g, cur);
         if (ocol >= 0) {
-            double* p0 = partial + (size_t)cta * 2 * T * C2 + ocol;
-            double* p1 = p0 + (size_t)T * C2;
 #pragma unroll
-            for (int n = 0; n < 32; n++) {
-                p0[(size_t)n * C2] = (double)hs0[n] + (double)hc0[n];
-                p1[(size_t)n * C2] = (double)hs1[n] + (double)hc1[n];
+            for (int o = 0; o < NO; o++) {
+                double* p = partial + ((size_t)cta * 2 + o0 + o) * T * C2 + ocol;
+#pragma unroll
+                for (int n = 0; n < 32; n++) p[(size_t)n * C2] = (double)hs[o][n] + (double)hc[o][n];
             }
         }
     }
@@ -714,29 +724,40 @@ TcJob job_of(mot_handle* h, long long step_i) {
 void launch_jobs(mot_handle* h0, TcJobs& jobs, int nctas, int max_npad, int cap, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     once_per_device(attr, h0->dev, [] {
-        cudaFuncSetAttribute(k_hist_tc<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-        cudaFuncSetAttribute(k_hist_tc<5, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-        cudaFuncSetAttribute(k_hist_tc<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-        cudaFuncSetAttribute(k_hist_tc<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-        cudaFuncSetAttribute(k_hist_tc<5, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
-        cudaFuncSetAttribute(k_hist_tc<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+        const int mx = (int)TC_SMEM_MAX;
+        cudaFuncSetAttribute(k_hist_tc<6, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<5, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<4, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<6, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<5, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<4, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<6, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<5, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<4, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<6, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<5, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_hist_tc<4, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     });
     // failure test of the bounded waits (mot_options.hist_stall_test), off by default
     const int stall = h0->opt.hist_stall_test > 0 ? h0->opt.hist_stall_test - 1 : -1;
     const int deepest = mot::history_tc_stages(max_npad, h0->tc_bulk, cap);
     const int ns = h0->tc_stages > 0 ? std::min(h0->tc_stages, deepest) : deepest;
-#define MOT_TC_LAUNCH(NSV, BV)                                                                              \
-    k_hist_tc<NSV, BV><<<nctas, TC_THREADS, TcLayout<NSV, BV>::bytes(max_npad, cap), s>>>(jobs, cap, stall, \
-                                                                                          1000000ull)
+    const bool e8 = h0->tc_epi == 8;
+#define MOT_TC_LAUNCH(NSV, BV, EWV)                                                                            \
+    k_hist_tc<NSV, BV, EWV><<<nctas, tc_threads<EWV>(), TcLayout<NSV, BV>::bytes(max_npad, cap), s>>>( \
+        jobs, cap, stall, 1000000ull)
+#define MOT_TC_LAUNCH_NS(BV, EWV)              \
+    if (ns == 6) MOT_TC_LAUNCH(6, BV, EWV);    \
+    else if (ns == 5) MOT_TC_LAUNCH(5, BV, EWV); \
+    else MOT_TC_LAUNCH(4, BV, EWV)
     if (h0->tc_bulk) {
-        if (ns == 6) MOT_TC_LAUNCH(6, true);
-        else if (ns == 5) MOT_TC_LAUNCH(5, true);
-        else MOT_TC_LAUNCH(4, true);
+        if (e8) MOT_TC_LAUNCH_NS(true, 8);
+        else MOT_TC_LAUNCH_NS(true, 4);
     } else {
-        if (ns == 6) MOT_TC_LAUNCH(6, false);
-        else if (ns == 5) MOT_TC_LAUNCH(5, false);
-        else MOT_TC_LAUNCH(4, false);
+        if (e8) MOT_TC_LAUNCH_NS(false, 8);
+        else MOT_TC_LAUNCH_NS(false, 4);
     }
+#undef MOT_TC_LAUNCH_NS
 #undef MOT_TC_LAUNCH
     h0->launches++;
 }

@@ -1125,52 +1125,109 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
             }
         }
     }
-    int64_t nt = 0;
-    for (auto& v : id)
-        if (v == -2) v = (int)nt++;
-    h->ntiles = nt;
-    h->max_tail_lag = max_tail;
-    std::vector<double> tiles((size_t)nt * T * T, 0.0);
-    // pass 2: fill (row-block ranges in parallel threads)
-    auto fill = [&](int tid, int nth) {
-        for (int mi = 0; mi < 12; mi++) {
-            const mot_lagmat& M = ops->mat[mi];
-            const int kind = kMatKind[mi];
-            const int fam = kKindFamily[kind];
-            const int lagmax = fam == 0 ? h->kmax : fam == 1 ? h->kmax + 1 : h->kmax - 1;
-            const bool tails = (mi == 5 || mi == 11) && M.tail_lag && M.tail_val;
-            for (int m = 0; m < h->ne && M.nent > 0; m++) {
-                const int p = h->iperm[m];
-                const int rb = p / T;
-                if (rb % nth != tid) continue;
-                const int r = p - rb * T;
-                for (int64_t e = M.rowptr[m]; e < M.rowptr[m + 1]; e++) {
-                    const int q = h->iperm[M.col[e]];
-                    const int qs = colpos[(size_t)rb * np + q];
-                    const int cb = qs / T, cc = qs - cb * T;
-                    for (int k = M.k0[e]; k < M.k0[e] + M.cnt[e] && k <= lagmax; k++) {
-                        const double v = M.val[M.voff[e] + (k - M.k0[e])];
-                        if (v == 0.0) continue;
-                        tiles[(size_t)id[key(kind, k, rb, cb)] * T * T + r * T + cc] += v;
-                    }
-                    if (tails) {
-                        const int a = M.tail_lag[e];
-                        const double v = M.tail_val[e];
-                        if (a >= 1 && a <= h->kmax - 1 && v != 0.0)
-                            tiles[(size_t)id[key(9, a, rb, cb)] * T * T + r * T + cc] += v;
-                    }
+    // Tile numbering: row block major, then (kind, lag, column block), so that
+    // the tiles of a range of row blocks are contiguous and can be filled on
+    // the host and uploaded range by range (the FP64 values of every tile
+    // are never held at once). The mixed path keeps FP64 copies of the lag-0
+    // tiles only (the dense Q_0 assembly reads them), in a compact numbering;
+    // every other tile goes to the device as FP32.
+    const bool mixed_tiles = h->opt.precision == MOT_PREC_MIXED && mflag(h, MOT_MIX_HIST32);
+    std::vector<int64_t> rb_first(nrb + 1, 0);
+    std::vector<int> lag0_slot;  // compact index of a lag-0 tile (mixed path), -1 otherwise
+    int64_t nt = 0, n0 = 0;
+    for (int rb = 0; rb < nrb; rb++) {
+        rb_first[rb] = nt;
+        for (int kind = 0; kind < NTK; kind++)
+            for (int k = 0; k < L; k++)
+                for (int cb = 0; cb < nrb; cb++) {
+                    int& v = id[key(kind, k, rb, cb)];
+                    if (v != -2) continue;
+                    v = (int)nt++;
+                    lag0_slot.push_back(k == 0 && kKindFamily[kind] != 3 ? (int)n0++ : -1);
                 }
-            }
-        }
-    };
-    int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> th;
-    for (int t = 0; t < nth; t++) th.emplace_back(fill, t, nth);
-    for (auto& t : th) t.join();
-    int64_t nz = 0;
+    }
+    rb_first[nrb] = nt;
+    h->ntiles = nt;
+    h->ntiles_fp64 = mixed_tiles ? n0 : nt;
+    h->max_tail_lag = max_tail;
+    const size_t TT = (size_t)T * T;
+    if (mixed_tiles) {
+        h->d_tiles = (double*)dalloc(h, sizeof(double) * std::max<int64_t>(1, n0) * TT);
+        h->d_tiles32 = (float*)dalloc(h, sizeof(float) * std::max<int64_t>(1, nt) * TT);
+        if (!h->d_tiles || !h->d_tiles32) return fail(h, MOT_EOOM, "device allocation (history tiles)");
+    } else {
+        h->d_tiles = (double*)dalloc(h, sizeof(double) * std::max<int64_t>(1, nt) * TT);
+        if (!h->d_tiles) return fail(h, MOT_EOOM, "device allocation (history tiles)");
+    }
+    // internal rows of every row block
     std::vector<int> tnnz(nt, 0);
-    for (int64_t t = 0; t < nt; t++)
-        for (int e = 0; e < T * T; e++) tnnz[t] += tiles[(size_t)t * T * T + e] != 0.0;
+    int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    const int64_t batch_tiles = 1 << 18;  // at most 2 GB of FP64 tiles on the host at a time
+    std::vector<double> buf;
+    std::vector<float> buf32;
+    int rb0 = 0;
+    while (rb0 < nrb) {
+        int rb1 = rb0 + 1;
+        while (rb1 < nrb && rb_first[rb1 + 1] - rb_first[rb0] <= batch_tiles) rb1++;
+        const int64_t t0 = rb_first[rb0], ntb = rb_first[rb1] - t0;
+        buf.assign((size_t)ntb * TT, 0.0);
+        // pass 2 over the rows of row blocks [rb0, rb1) (threads split the row blocks)
+        auto fill = [&](int tid) {
+            for (int mi = 0; mi < 12; mi++) {
+                const mot_lagmat& M = ops->mat[mi];
+                const int kind = kMatKind[mi];
+                const int fam = kKindFamily[kind];
+                const int lagmax = fam == 0 ? h->kmax : fam == 1 ? h->kmax + 1 : h->kmax - 1;
+                const bool tails = (mi == 5 || mi == 11) && M.tail_lag && M.tail_val;
+                if (M.nent == 0) continue;
+                for (int rb = rb0 + tid; rb < rb1; rb += nth)
+                    for (int p = rb * T; p < std::min(h->ne, rb * T + T); p++) {
+                        const int m = h->perm[p];
+                        const int r = p - rb * T;
+                        for (int64_t e = M.rowptr[m]; e < M.rowptr[m + 1]; e++) {
+                            const int q = h->iperm[M.col[e]];
+                            const int qs = colpos[(size_t)rb * np + q];
+                            const int cb = qs / T, cc = qs - cb * T;
+                            for (int k = M.k0[e]; k < M.k0[e] + M.cnt[e] && k <= lagmax; k++) {
+                                const double v = M.val[M.voff[e] + (k - M.k0[e])];
+                                if (v == 0.0) continue;
+                                buf[(size_t)(id[key(kind, k, rb, cb)] - t0) * TT + r * T + cc] += v;
+                            }
+                            if (tails) {
+                                const int a = M.tail_lag[e];
+                                const double v = M.tail_val[e];
+                                if (a >= 1 && a <= h->kmax - 1 && v != 0.0)
+                                    buf[(size_t)(id[key(9, a, rb, cb)] - t0) * TT + r * T + cc] += v;
+                            }
+                        }
+                    }
+            }
+        };
+        {
+            std::vector<std::thread> th;
+            for (int t = 0; t < nth; t++) th.emplace_back(fill, t);
+            for (auto& t : th) t.join();
+        }
+        for (int64_t t = 0; t < ntb; t++)
+            for (size_t e = 0; e < TT; e++) tnnz[t0 + t] += buf[(size_t)t * TT + e] != 0.0;
+        if (mixed_tiles) {
+            buf32.resize(buf.size());
+            for (size_t e = 0; e < buf.size(); e++) buf32[e] = (float)buf[e];
+            CK(cudaMemcpy(h->d_tiles32 + (size_t)t0 * TT, buf32.data(), sizeof(float) * buf32.size(),
+                          cudaMemcpyHostToDevice));
+            for (int64_t t = 0; t < ntb; t++)
+                if (lag0_slot[t0 + t] >= 0)
+                    CK(cudaMemcpy(h->d_tiles + (size_t)lag0_slot[t0 + t] * TT, buf.data() + (size_t)t * TT,
+                                  sizeof(double) * TT, cudaMemcpyHostToDevice));
+        } else if (ntb > 0) {
+            CK(cudaMemcpy(h->d_tiles + (size_t)t0 * TT, buf.data(), sizeof(double) * buf.size(),
+                          cudaMemcpyHostToDevice));
+        }
+        rb0 = rb1;
+    }
+    std::vector<double>().swap(buf);
+    std::vector<float>().swap(buf32);
+    int64_t nz = 0;
     for (int64_t t = 0; t < nt; t++) nz += tnnz[t];
     h->tile_fill = nt ? (double)nz / ((double)nt * T * T) : 0.0;
     std::vector<char> used_hist(nt, 0);
@@ -1187,6 +1244,7 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
                     auto push = [&](int part, int outi) {
                         HistTask tk{t, cb, k, part | (var << 2) | (outi << 4)};
                         if (k == 0 && fam != 3) {
+                            if (mixed_tiles) tk.tile = lag0_slot[t];  // the compact FP64 lag-0 tiles
                             th_lag0.push_back(tk);
                             rb_lag0.push_back(rb);
                         } else {
@@ -1262,9 +1320,6 @@ int build_tiles(mot_handle* h, const mot_operators* ops) {
         h->tc_tasks_host = std::move(th_hist);  // kept for re-chunking by the tuner
         h->tc_rbs_host = std::move(rb_hist);
     }
-    h->d_tiles = (double*)dalloc(h, sizeof(double) * std::max<size_t>(1, tiles.size()));
-    if (!h->d_tiles) return fail(h, MOT_EOOM, "device allocation (history tiles)");
-    if (!tiles.empty()) CK(cudaMemcpy(h->d_tiles, tiles.data(), sizeof(double) * tiles.size(), cudaMemcpyHostToDevice));
     return MOT_OK;
 }
 
@@ -1287,10 +1342,7 @@ int precompute_mixed(mot_handle* h) {
     h->d_LF = (double*)dalloc(h, sizeof(double) * (size_t)h->npad * n2);
     h->d_Q0f = (float*)dalloc(h, sizeof(float) * (size_t)n2 * n2);
     h->d_LFf = (float*)dalloc(h, sizeof(float) * (size_t)h->npad * n2);
-    const bool h32 = (h->opt.mixed_flags & MOT_MIX_HIST32) != 0;
-    if (h32)
-        h->d_tiles32 =
-            (float*)dalloc(h, sizeof(float) * (size_t)std::max<int64_t>(1, h->ntiles) * MOT_TILE * MOT_TILE);
+    const bool h32 = (h->opt.mixed_flags & MOT_MIX_HIST32) != 0;  // FP32 tiles written by build_tiles
     if (!h->d_Q0 || !h->d_LF || !h->d_Q0f || !h->d_LFf || (h32 && !h->d_tiles32))
         return fail(h, MOT_EOOM, "device allocation (mixed-precision operators)");
     CK(cudaMemsetAsync(h->d_cg_iters, 0, 2 * sizeof(int), s));
@@ -1306,7 +1358,6 @@ int precompute_mixed(mot_handle* h) {
     }
     launch_d2f(h, (size_t)n2 * n2, h->d_Q0, h->d_Q0f, s);
     launch_d2f(h, (size_t)h->npad * n2, h->d_LF, h->d_LFf, s);
-    if (h32) launch_d2f(h, (size_t)h->ntiles * MOT_TILE * MOT_TILE, h->d_tiles, h->d_tiles32, s);
     if (h->opt.mixed_flags & MOT_MIX_PRECOND) {
         // GMRES preconditioner: Q_0^{-1} by LU with partial pivoting (FP64), kept in FP32
         double* lu = (double*)dalloc(h, sizeof(double) * (size_t)n2 * n2);
@@ -1376,9 +1427,10 @@ int precompute_mixed(mot_handle* h) {
             return st;
         CK(cudaDeviceSynchronize());
     }
-    if (h32) {  // the FP64 history tiles are no longer read
+    if (h32) {  // the FP64 lag-0 tiles (the dense Q_0 assembly's input) are no longer read
         cudaFree(h->d_tiles);
-        h->device_bytes -= (int64_t)(sizeof(double) * (size_t)std::max<int64_t>(1, h->ntiles) * MOT_TILE * MOT_TILE);
+        h->device_bytes -=
+            (int64_t)(sizeof(double) * (size_t)std::max<int64_t>(1, h->ntiles_fp64) * MOT_TILE * MOT_TILE);
         h->d_tiles = nullptr;
     }
     return MOT_OK;
@@ -1622,7 +1674,7 @@ int tune_tc(mot_handle* const* hs, int n, cudaStream_t s) {
     }
     const bool bulk = hs[0]->tc_bulk;
     float best = 1e30f;
-    int bcap = MOT_TC_CHUNK, bns = 0;
+    int bcap = MOT_TC_CHUNK, bns = 0, bepi = 4;
     double blf = 0.4;
     const int caps[] = {256, 512, 1024};
     const double fracs[] = {0.2, 0.4, 0.8};
@@ -1636,27 +1688,34 @@ int tune_tc(mot_handle* const* hs, int n, cudaStream_t s) {
             }
             int listcap = 1;
             for (int k = 0; k < n; k++) listcap = std::max(listcap, hs[k]->hist_tc_list.cap);
-            for (int ns = 4; ns <= 6; ns++) {
-                if (ns > history_tc_stages(max_npad, bulk, listcap)) continue;
-                for (int k = 0; k < n; k++) hs[k]->tc_stages = ns;
-                launch_history_tc_many(hs, n, s1.data(), s2.data(), s, false);
-                float t[3];
-                for (int r = 0; r < 3; r++) t[r] = launch_history_tc_many(hs, n, s1.data(), s2.data(), s, true);
-                std::sort(t, t + 3);
-                if (cudaGetLastError() != cudaSuccess) return fail(hs[0], MOT_ECUDA, "mot_tune: trial launch failed");
-                if (t[1] < best) {
-                    best = t[1];
-                    bcap = cap;
-                    blf = lf;
-                    bns = ns;
+            for (int ns = 4; ns <= 6; ns++)
+                for (int epi = 4; epi <= 8; epi += 4) {
+                    if (ns > history_tc_stages(max_npad, bulk, listcap)) continue;
+                    for (int k = 0; k < n; k++) {
+                        hs[k]->tc_stages = ns;
+                        hs[k]->tc_epi = epi;
+                    }
+                    launch_history_tc_many(hs, n, s1.data(), s2.data(), s, false);
+                    float t[3];
+                    for (int r = 0; r < 3; r++) t[r] = launch_history_tc_many(hs, n, s1.data(), s2.data(), s, true);
+                    std::sort(t, t + 3);
+                    if (cudaGetLastError() != cudaSuccess)
+                        return fail(hs[0], MOT_ECUDA, "mot_tune: trial launch failed");
+                    if (t[1] < best) {
+                        best = t[1];
+                        bcap = cap;
+                        blf = lf;
+                        bns = ns;
+                        bepi = epi;
+                    }
                 }
-            }
         }
     for (int k = 0; k < n; k++) {
         int st;
         if ((st = make_tc_list(hs[k], hs[k]->tc_tasks_host, hs[k]->tc_rbs_host, bcap, blf)) != MOT_OK) return st;
         if ((st = fit_partial(hs[k])) != MOT_OK) return st;
         hs[k]->tc_stages = bns;
+        hs[k]->tc_epi = bepi;
         hs[k]->tc_tuned = true;
         hs[k]->tc_tune_ms = best;
     }
@@ -2018,6 +2077,7 @@ MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
     info->tc_chunk_cap = h->tc_cap;
     info->tc_lag_frac = h->tc_lag_frac;
     info->tc_stages = h->tc_stages;
+    info->tc_epilogue_warps = h->tc_epi;
     info->tc_tuned = h->tc_tuned ? 1 : 0;
     info->tc_tune_ms = h->tc_tune_ms;
     info->tc_launches = h->tc_launches;

@@ -103,8 +103,9 @@ struct mot_handle {
     double* d_rhs_wf = nullptr;
 
     // block-sparse history
-    double* d_tiles = nullptr;
+    double* d_tiles = nullptr;     // FP64 tiles (mixed path: lag 0 only, compact numbering, until set-up ends)
     int64_t ntiles = 0;
+    int64_t ntiles_fp64 = 0;       // tiles held in FP64 (all; on the mixed path only those of lag 0)
     double tile_fill = 0;
     TaskList hist, lag0;
     TaskList hist_tc_list;  // tensor-core history: chunks = (lag range, row block) pieces, lag range major
@@ -171,6 +172,7 @@ struct mot_handle {
     bool tc_bulk = false;          // tensor-core history in the bulk form (global column order, blocked ring)
     int tc_stages = 0;             // pipeline depth of the tensor-core history (0: the deepest that fits)
     int tc_cap = 0;                // tasks per chunk the tensor-core list was cut with
+    int tc_epi = 4;                // epilogue warps of the tensor-core history (4 or 8)
     double tc_lag_frac = 0;        // fraction of L2 a lag range of the list may fill
     bool tc_tuned = false;         // the three were chosen by mot_tune
     float tc_tune_ms = 0;          // the chosen configuration's launch time in the tuning (ms)

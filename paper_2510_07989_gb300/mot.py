@@ -69,7 +69,8 @@ class mot_info(ctypes.Structure):
                 ("hist_kernel", ctypes.c_int32), ("hist_tc_tasks", ctypes.c_int64),
                 ("gmres_iters_total", ctypes.c_int64), ("tc_chunk_cap", ctypes.c_int32),
                 ("tc_lag_frac", ctypes.c_double), ("tc_stages", ctypes.c_int32), ("tc_tuned", ctypes.c_int32),
-                ("tc_tune_ms", ctypes.c_double), ("tc_launches", ctypes.c_int64)]
+                ("tc_tune_ms", ctypes.c_double), ("tc_launches", ctypes.c_int64),
+                ("tc_epilogue_warps", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
