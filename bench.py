@@ -205,9 +205,10 @@ class Clocks:
 # taken on (kernel_source_sha: comments and the host launch code excluded): a
 # changed kernel reports null until the counters are taken again.
 TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-    #     --clock-control none -k regex:k_hist_tc -s 56 -c 1 python bench.py --steps 2 --warmup 1 --no-cpu-baseline
-    ("k_hist_tc", "torus64x24"): (47718425000 + 231234304, "b1cf639947bd1b231c71c62365fa2df7f5a3c7b2"),
+    # ncu --profile-from-start off --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+    #     --clock-control none -k regex:k_hist_tc -c 1
+    #     python bench.py --steps 2 --warmup 1 --no-cpu-baseline --fp64-steps 0
+    ("k_hist_tc", "torus64x24"): (32052556288 + 466490368, "329b400539ebe4094959123d37e4328d39602c3c"),
 }
 
 
@@ -317,14 +318,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def march_arm(M, torch, ops, exc, args, local, world, precision, steps, warmup, clocks=None, keep_waves=()):
-    """One measured arm: K + 1 + warmup untimed steps (full-depth history);
-    then `steps` steps through the public call with host buffers (waves in,
-    w_i out every step), timed end to end; then `steps` steps timed with CUDA
-    events on the launching stream (barrier + synchronize on both sides). The
-    caller centres the waves' pulse in the device-timed window. The steps of
-    keep_waves up to the end of the host-buffer window are returned for an
-    oracle check of its last step."""
+def march_arm(M, torch, ops, exc, args, local, world, precision, steps, warmup, clocks=None, keep_waves=(),
+              state_in=None, hand_over=False):
+    """One measured arm: K + 1 + warmup untimed steps (full-depth history) --
+    or, with state_in, the march state another arm handed over (mot_save_state)
+    and one untimed step from it, whose w_i is returned; then `steps` steps
+    through the public call with host buffers (waves in, w_i out every step),
+    timed end to end; then `steps` steps timed with CUDA events on the
+    launching stream (barrier + synchronize on both sides). The caller centres
+    the waves' pulse in the device-timed window. The steps of keep_waves up to
+    the end of the host-buffer window are returned for an oracle check of its
+    last step. With hand_over, the state at the end of the host-buffer window
+    is saved and one more untimed step taken before the device-timed window:
+    the pair lets the next arm's first step be compared with this one's from
+    the same state."""
     B = exc.B
     K = ops.kmax + 1
     kw = dict(device=local, timing=1, precision=precision)
@@ -346,12 +353,19 @@ def march_arm(M, torch, ops, exc, args, local, world, precision, steps, warmup, 
         for b in keep_waves:
             hist[b][i] = host_out.numpy()[b].reshape(-1).copy()
 
-    n_pre = K + 1 + warmup
-    for i in range(1, n_pre + 1):
-        M.mot_step(s.h, waves, B, host_out.numpy() if keep_waves else None, stream)
-        keep(i)
-        if i == K + 1 and precision == M.MOT_PREC_MIXED and M.mot_get_info(s.h)["hist_kernel"] == 2:
-            M.mot_tune([s.h], stream)  # the history kernel's configuration, chosen at full depth
+    first = None
+    if state_in is not None:
+        M.mot_load_state(s.h, state_in)
+        M.mot_step(s.h, waves, B, host_out.numpy(), stream)
+        first = host_out.numpy().copy()
+        n_pre = M.mot_get_info(s.h)["step"]
+    else:
+        n_pre = K + 1 + warmup
+        for i in range(1, n_pre + 1):
+            M.mot_step(s.h, waves, B, host_out.numpy() if keep_waves else None, stream)
+            keep(i)
+            if i == K + 1 and precision == M.MOT_PREC_MIXED and M.mot_get_info(s.h)["hist_kernel"] == 2:
+                M.mot_tune([s.h], stream)  # the history kernel's configuration, chosen at full depth
 
     def barrier():
         if world > 1:
@@ -362,12 +376,19 @@ def march_arm(M, torch, ops, exc, args, local, world, precision, steps, warmup, 
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    peak = np.zeros(B)  # largest step norm of every wave in the host-buffer window
     for i in range(n_pre + 1, n_pre + steps + 1):
         M.mot_step(s.h, waves, B, host_out.numpy(), stream)
         keep(i)
+        peak = np.maximum(peak, np.linalg.norm(host_out.numpy(), axis=(1, 2)))
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
+    state, after = None, None
+    if hand_over:  # on the rising pulse, at the largest step norm so far
+        state = M.mot_save_state(s.h)
+        M.mot_step(s.h, waves, B, host_out.numpy(), stream)
+        after = host_out.numpy().copy()
     info0 = M.mot_get_info(s.h)
     barrier()
     torch.cuda.synchronize()
@@ -390,7 +411,7 @@ def march_arm(M, torch, ops, exc, args, local, world, precision, steps, warmup, 
     ms = ev0.elapsed_time(ev1)
     info1 = M.mot_get_info(s.h)
     return dict(s=s, ms=ms, e2e_ms=e2e_s * 1e3, info0=info0, info1=info1, t_load=t_load, check_step=n_pre + steps,
-                hist=hist, noconv=s.noconv)
+                hist=hist, noconv=s.noconv, state=state, after=after, first=first, peak=peak)
 
 
 def roofline_of(info0, info1, ms_step, steps, workload, peaks, how):
@@ -457,7 +478,8 @@ def run_ours(args):
     clocks = Clocks(local)
     clocks.start()  # running before the warm-up, so that it samples the whole timed region
     A = march_arm(M, torch, ops, exc, args, local, world, primary, args.steps, args.warmup, clocks,
-                  keep_waves=(0,) if world == 1 and not args.no_cpu_baseline else ())
+                  keep_waves=(0,) if world == 1 and not args.no_cpu_baseline else (),
+                  hand_over=primary == M.MOT_PREC_MIXED and args.fp64_steps > 0)
     ck = clocks.stop()
     ms_max, e2e_ms_max = reduce_max([A["ms"], A["e2e_ms"]], world)
     value = throughput(world, B, args.steps, ms_max)
@@ -469,11 +491,17 @@ def run_ours(args):
     fp64 = None
     if primary == M.MOT_PREC_MIXED and args.fp64_steps > 0:
         n64 = args.fp64_steps
-        exc64 = make_waves(args.workload, rank, K + 1 + args.warmup + 1.5 * n64)
-        F = march_arm(M, torch, ops, exc64, args, local, world, M.MOT_PREC_FP64, n64, args.warmup)
+        # the FP64 arm continues the same march from the mixed arm's state (no
+        # prefill of its own); its first step, from that common state, against
+        # the mixed arm's step gives the accuracy of one mixed step on the pulse
+        F = march_arm(M, torch, ops, exc, args, local, world, M.MOT_PREC_FP64, n64, args.warmup,
+                      state_in=A["state"])
         f_ms, f_e2e = reduce_max([F["ms"], F["e2e_ms"]], world)
         fi0, fi1 = F["info0"], F["info1"]
         F.pop("s")
+        wm, wf = A["after"], F["first"]
+        step_rel = np.linalg.norm(wm - wf, axis=(1, 2)) / np.linalg.norm(wf, axis=(1, 2))
+        peak_rel = np.linalg.norm(wm - wf, axis=(1, 2)) / np.maximum(A["peak"], 1e-300)
         fp64 = {"value": throughput(world, B, n64, f_ms), "unit": "RHS·steps/s", "steps": n64,
                 "ms_per_step": f_ms / n64, "dtype": "f64",
                 "solver": "right-preconditioned GMRES, Q_0 in FP64 product form, M = FP64 dense Q_0^-1",
@@ -481,6 +509,14 @@ def run_ours(args):
                 "e2e": {"value": throughput(world, B, n64, f_e2e), "unit": "RHS·steps/s",
                         "h2d_bytes_per_step": 80 * B, "d2h_bytes_per_step": 8 * 2 * ops.ne * B},
                 "load_s": round(F["t_load"], 1), "steps_not_converged": F["noconv"],
+                "prefill": "none: the mixed arm's march state (mot_save_state / mot_load_state)",
+                "mixed_vs_fp64_one_step": {"step": F["info0"]["step"] - n64, "waves": int(wm.shape[0]),
+                                           "max_rel_err_2norm": float(step_rel.max()),
+                                           "median_rel_err_2norm": float(np.median(step_rel)),
+                                           "max_rel_err_vs_wave_peak": float(peak_rel.max()),
+                                           "wave_peak": "largest step norm of the wave in the mixed arm's "
+                                                        "host-buffer window, which ends at the common state "
+                                                        "(on the rising pulse)"},
                 "roofline": roofline_of(fi0, fi1, f_ms / n64, n64, args.workload, *measured_peaks())}
         del F
     if rank != 0:

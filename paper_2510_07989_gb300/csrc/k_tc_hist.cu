@@ -470,20 +470,39 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
         // releases it (one arrival per epilogue warp)
         auto fold = [&](uint32_t col, float c, int o, bool release, int b) {
             float va[32], vb[32];
-            tmem_ld32(col + 64, va);   // terms of relative size 2^-8
-            tmem_ld32(col + 128, vb);  // and 2^-16
-            tmem_wait_ld();
+            if constexpr (EW == 8) {
+                // one output per warp: the three blocks in one round trip of
+                // TMEM loads, then the buffer is released before the arithmetic
+                float vl[32];
+                tmem_ld32(col + 64, va);   // terms of relative size 2^-8
+                tmem_ld32(col + 128, vb);  // and 2^-16
+                tmem_ld32(col, vl);        // the leading products
+                tmem_wait_ld();
+                if (release) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(ACCE(b));
+                }
 #pragma unroll
-            for (int n = 0; n < 32; n++) hc[o][n] += c * (va[n] + vb[n]);
-            tmem_ld32(col, va);  // the leading products
-            tmem_wait_ld();
-            if (release) {
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(ACCE(b));
+                for (int n = 0; n < 32; n++) hc[o][n] += c * (va[n] + vb[n]);
+#pragma unroll
+                for (int n = 0; n < 32; n++) two_sum(hs[o][n], hc[o][n], c * vl[n]);
+            } else {
+                tmem_ld32(col + 64, va);   // terms of relative size 2^-8
+                tmem_ld32(col + 128, vb);  // and 2^-16
+                tmem_wait_ld();
+#pragma unroll
+                for (int n = 0; n < 32; n++) hc[o][n] += c * (va[n] + vb[n]);
+                tmem_ld32(col, va);  // the leading products
+                tmem_wait_ld();
+                if (release) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(ACCE(b));
+                }
+#pragma unroll
+                for (int n = 0; n < 32; n++) two_sum(hs[o][n], hc[o][n], c * va[n]);
             }
-#pragma unroll
-            for (int n = 0; n < 32; n++) two_sum(hs[o][n], hc[o][n], c * va[n]);
         };
         auto drain = [&](int gg, int key) -> bool {
             const int b = gg % NB;

@@ -42,6 +42,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about `ns` nanoseconds pass, instead of spinning on the issue
+// slots the working warps of its sub-partition need.
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Slow path of a bounded wait: gives up when the CTA's abort flag is set or
 // after `bound` ns (then it raises the flag and records `code` in *err).
 static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
@@ -60,9 +75,11 @@ static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity
 }
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
                                           int code, unsigned long long bound = WAIT_NS) {
+    // fast path: up to 1024 tries of at most ~1 us of suspension each (~1 ms),
+    // then the time-bounded slow path
 #pragma unroll 1
-    for (int i = 0; i < 4096; i++)
-        if (mbar_try(bar, parity)) return true;
+    for (int i = 0; i < 1024; i++)
+        if (mbar_try_sleep(bar, parity, 1000u)) return true;
     return mbar_wait_slow(bar, parity, abort_flag, err, code, bound);
 }
 // Wait used while shutting down: bounded, ignores the abort flag.
