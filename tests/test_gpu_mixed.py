@@ -132,6 +132,31 @@ def test_tensor_core_history_bulk_form(M, torus_small, B):
     assert np.abs(W - Wg).max() < TOL_MIXED * np.abs(Wg).max()
 
 
+def test_tune_keeps_the_march(M, torus_small):
+    """mot_tune on one handle at full depth (step 54 of the 53-lag torus):
+    a configuration is chosen and reported, and the march it continues meets
+    the oracle as before (its trial launches leave the march state alone)."""
+    ops, S = torus_small
+    exc = MS.fibonacci_batch(64, ops.dt, w_steps=30, t0_steps=60)
+    waves = M.mot_waves(exc)
+    n = 130
+    s = M.Solver(ops, precision=M.MOT_PREC_MIXED)
+    out = np.zeros((64, 2, ops.ne))
+    W = np.zeros((n, 64, 2, ops.ne))
+    for i in range(n):
+        if i == ops.kmax + 1:
+            M.mot_tune([s.h])
+        M.mot_step(s.h, waves, 64, out)
+        W[i] = out
+    info = s.info()
+    assert info["tc_tuned"] == 1 and info["tc_chunk_cap"] in (256, 512, 1024) and info["tc_stages"] in (4, 5, 6)
+    assert info["tc_epilogue_warps"] in (4, 8) and info["tc_tune_ms"] > 0
+    errs = [rel(W[:, b].reshape(n, -1), O.march(S, exc, n, b=b)) for b in (0, 63)]
+    print(f"tuned march (cap {info['tc_chunk_cap']}, lag fraction {info['tc_lag_frac']}, {info['tc_stages']} stages, "
+          f"{info['tc_epilogue_warps']} epilogue warps): rel errs", ["%.3e" % e for e in errs])
+    assert max(errs) < TOL_MIXED
+
+
 def test_mixed_save_load_state_resumes_exactly(M, torus_small):
     """mot_save_state / mot_load_state on the mixed path (reduced-precision ring
     copies rebuilt from the FP64 ring): the resumed run repeats the original."""

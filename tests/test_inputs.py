@@ -211,3 +211,26 @@ def test_time_bases_against_the_paper_definitions():
         for xi in (-1.3 * dt, -0.6 * dt, 0.0, 0.25 * dt, 0.9 * dt):
             lhs = integral(lambda t: p0(t - i * dt) * p0(t + xi), (i - 1) * dt, i * dt, (-xi, -dt - xi)) / dt
             assert abs(lhs - h0(i * dt + xi)) < 1e-12
+
+
+def test_uneven_batch_recipe():
+    """The uneven 24-scatterer batch: icospheres L1-L3 first, then 21
+    ellipsoids with 540..7260 unknowns (geodesic frequency 3..11), semi-axes
+    within [0.5, 1.5] (the diameter at most 3), eps_r within [1.5, 8];
+    deterministic for a seed, different for another."""
+    from paper_2510_07989_gb300.inputs import meshes as MS
+    b = MS.uneven_batch(24)
+    assert len(b) == 24
+    assert [2 * m.ne for m, _ in b[:3]] == [240, 960, 3840]
+    for m, eps in b:
+        assert 1.5 <= eps <= 8.0
+        assert m.nv - m.ne + m.nf == 2  # closed genus-0 surfaces
+    for m, _ in b[3:]:
+        n2 = 2 * m.ne
+        assert 540 <= n2 <= 7260 and (n2 // 60) in {k * k for k in range(3, 12)}
+        assert MS.diameter(m) <= 3.0 + 1e-9
+    again = MS.uneven_batch(24)
+    assert all(np.array_equal(m.verts, m2.verts) and e == e2 for (m, e), (m2, e2) in zip(b, again))
+    other = MS.uneven_batch(24, seed=1)
+    assert any(not np.array_equal(m.verts, m2.verts) for (m, _), (m2, _) in zip(b[3:], other[3:]) if m.nv == m2.nv) \
+        or [m.nv for m, _ in b] != [m.nv for m, _ in other]
