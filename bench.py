@@ -537,7 +537,8 @@ def run_ours(args):
                        "history_prefill_steps": K + 1,
                        "tc_form": args.tc_form,
                        "tuner": {"chunk_cap": info1["tc_chunk_cap"], "lag_frac": info1["tc_lag_frac"],
-                                 "stages": info1["tc_stages"], "epilogue_warps": info1["tc_epilogue_warps"],
+                                 "stages": info1["tc_stages"], "tasks_per_stage": info1["tc_tasks_per_stage"],
+                                 "epilogue_warps": info1["tc_epilogue_warps"],
                                  "tuned": bool(info1["tc_tuned"]),
                                  "tuned_launch_ms": info1["tc_tune_ms"]},
                        "history_launches_before_timed": info0["tc_launches"],
@@ -704,7 +705,8 @@ def run_uneven(args):
                        "eps_r": [round(e, 3) for _, e in specs], "c_dt": UNEVEN_DT, "rhs_per_scatterer": UNEVEN_B,
                        "history_lags_max": K, "tc_form": args.tc_form,
                        "tuner": {"chunk_cap": info1[0]["tc_chunk_cap"], "lag_frac": info1[0]["tc_lag_frac"],
-                                 "stages": info1[0]["tc_stages"], "epilogue_warps": info1[0]["tc_epilogue_warps"],
+                                 "stages": info1[0]["tc_stages"], "tasks_per_stage": info1[0]["tc_tasks_per_stage"],
+                                 "epilogue_warps": info1[0]["tc_epilogue_warps"],
                                  "tuned": bool(info1[0]["tc_tuned"]),
                                  "tuned_launch_ms": info1[0]["tc_tune_ms"]},
                        "assembly_s": round(t_asm, 1), "load_s": round(t_load, 1),

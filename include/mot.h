@@ -97,7 +97,8 @@ typedef struct {
                               a few. Costs (2 npad)^2 doubles of device memory. */
     int32_t hist_stall_test; /* testing of the failure path only; 0 (default) = off. k > 0:
                               every tensor-core history launch withholds the copies of the
-                              k-th task of its first CTA, whose pipeline waits then give up
+                              k-th pipeline stage of its first CTA (the k-th task with one
+                              task per stage), whose pipeline waits then give up
                               after 1 ms; that CTA stops, drains its copies, releases TMEM
                               and raises the error word, and mot_step returns MOT_ECUDA
                               with the GPU context intact. */
@@ -205,7 +206,7 @@ typedef struct {
     int64_t gmres_iters_total;
     /* tensor-core history: the configuration in use -- tasks per chunk, the
        fraction of the L2 one lag range of the task list may fill, pipeline
-       depth (0: the deepest that fits) -- whether mot_tune (or mot_run_many)
+       stages (0: the deepest that fits) -- whether mot_tune (or mot_run_many)
        chose it, and its launch time in that tuning (ms) */
     int32_t tc_chunk_cap;
     double tc_lag_frac;
@@ -218,6 +219,10 @@ typedef struct {
     /* epilogue warps of the tensor-core history (4, or 8: two per TMEM lane
        quarter, one output each); a tuning choice like the three above */
     int32_t tc_epilogue_warps;
+    /* tasks per pipeline stage of the tensor-core history (1, or 2: the stage
+       holds two tasks' operands behind one full / empty barrier pair); a
+       tuning choice like the others */
+    int32_t tc_tasks_per_stage;
 } mot_info;
 
 /*
@@ -303,8 +308,9 @@ int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* cons
  * counterpart; it only picks how the work of Eq. (MOT)'s history sum is cut).
  * For n handles marched together (n = 1: one handle alone; n <= 32), every
  * candidate configuration -- tasks per chunk in {256, 512, 1024}, fraction of
- * the L2 a lag range may fill in {0.2, 0.4, 0.8}, pipeline depth in {4, 5, 6}
- * where it fits, epilogue warps in {4, 8} -- is applied and its launch (one
+ * the L2 a lag range may fill in {0.2, 0.4, 0.8}, pipeline stages x tasks
+ * per stage in {4 x 1, 5 x 1, 2 x 2, 3 x 2} where they fit in shared memory,
+ * epilogue warps in {4, 8} -- is applied and its launch (one
  * for all n handles) timed
  * three times with CUDA events on `stream` after one warm-up; the fastest
  * (median) is kept by every handle and reported by mot_get_info. The trial
@@ -315,6 +321,20 @@ int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* cons
  * the first step that contracts every member's full history.
  */
 int mot_tune(mot_handle* const* hs, int n, void* stream);
+
+/*
+ * Applies one configuration of the tensor-core history contraction without
+ * timing any (e.g. one mot_tune chose for the same mesh and batch before):
+ * tasks per chunk cap in [1, 1024], lag_frac in (0, 1], (stages,
+ * tasks_per_stage) one of (4, 1), (5, 1), (2, 2), (3, 2), epilogue_warps 4
+ * or 8. Only how the work of Eq. (MOT)'s history sum is cut changes; every
+ * configuration computes the same sums. Same requirements as mot_tune
+ * (MOT_ESTATE otherwise); MOT_EINVAL for a value out of range or a
+ * configuration whose pipeline does not fit in shared memory (the handle's
+ * previous configuration is then replaced by the chunking of cap and
+ * lag_frac with its old pipeline). mot_get_info reports it with tc_tuned 0.
+ */
+int mot_set_tc_config(mot_handle* h, int cap, double lag_frac, int stages, int tasks_per_stage, int epilogue_warps);
 
 /* Recovered currents of the last step, [B][4][ne]: j loop, j star, m loop,
  * m star (Eq. (dis_jm)), host or device memory. Ordered after the handle's

@@ -132,14 +132,24 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// s + c += v with the rounding error of s + v kept in c (Knuth's TwoSum).
-__device__ __forceinline__ void two_sum(float& s, float& c, float v) {
-    const float t = s + v;
-    const float bp = t - s;
-    const float e = (s - (t - bp)) + (v - bp);
+// Packed FP32 pairs: sm_100-family SMs issue one add, multiply or fma for
+// two FP32 lanes (same IEEE round-to-nearest result per lane), which halves
+// the instructions of the epilogue's compensated sums.
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as fma(b, -1, a): the product is exact, so one rounding as for a - b
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// s + c += v with the rounding error of s + v kept in c (Knuth's TwoSum), on
+// both lanes of a pair
+__device__ __forceinline__ void two_sum2(float2& s, float2& c, float2 v) {
+    const float2 t = f2add(s, v);
+    const float2 bp = f2sub(t, s);
+    const float2 e = f2add(f2sub(s, f2sub(t, bp)), f2sub(v, bp));
     s = t;
-    c += e;
+    c = f2add(c, e);
 }
+__device__ __forceinline__ float2 pair_of(const float (&v)[32], int n) { return make_float2(v[2 * n], v[2 * n + 1]); }
 
 __device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -153,15 +163,19 @@ __device__ __forceinline__ int pk_code(uint4 d) { return (int)(d.z >> 26); }
 // windowed sums (used as stored).
 __device__ __forceinline__ int task_xform(int code) { return (code & 3) == 2 ? 3 : (code >> 2) & 3; }
 
-template <int NS, bool BULK>
+// NS pipeline stages of TP tasks each (one FULL / EMPTY barrier pair per stage).
+template <int NS, bool BULK, int TP>
 struct TcLayout {
+    // the gathered form with one task per stage stages the row block's column
+    // order in shared memory; with two it reads it through L1 (room for stages)
+    static constexpr bool SCOL = !BULK && TP == 1;
     static constexpr int NBARS = 2 * NS + 2 * NB + 1;  // + one barrier for the final MMA drain
-    static constexpr size_t BARS = (size_t)NS * STAGE;
+    static constexpr size_t BARS = (size_t)NS * TP * STAGE;
     static constexpr size_t SLOT = BARS + ((8 * NBARS + 15) / 16) * 16;  // TMEM address, abort flag, issued count
     static constexpr size_t DESC = SLOT + 16;  // the chunk's packed tasks (uint4), cap of them
-    // then, in the gathered form, the column order of the row block (uint16)
+    // then (SCOL) the column order of the row block (uint16)
     static size_t bytes(int npad, int cap) {
-        return DESC + 16 * (size_t)cap + (BULK ? 0 : (((size_t)npad * 2 + 15) / 16) * 16) + 1024;
+        return DESC + 16 * (size_t)cap + (SCOL ? (((size_t)npad * 2 + 15) / 16) * 16 : 0) + 1024;
     }
     static_assert(BARS % 1024 == 0 && SLOT % 16 == 0 && DESC % 16 == 0,
                   "shared-memory regions must keep their alignment (uint4 task loads)");
@@ -206,11 +220,12 @@ struct TcJobs {
     TcJob job[MOT_TC_MAX_JOBS];
 };
 
-template <int NS, bool BULK, int EW>
+template <int NS, bool BULK, int EW, int TP>
 __global__ void __launch_bounds__(tc_threads<EW>(), 1)
     k_hist_tc(const __grid_constant__ TcJobs jobs, int cap, int stall_task, unsigned long long stall_bound) {
     constexpr int TC_THREADS = tc_threads<EW>();
-    using L = TcLayout<NS, BULK>;
+    using L = TcLayout<NS, BULK, TP>;
+    constexpr uint32_t SSTAGE = TP * STAGE;  // bytes of one pipeline stage (TP task slots of STAGE bytes)
     int jb = 0;
     while (jb + 1 < jobs.njobs && (int)blockIdx.x >= jobs.job[jb].cend) jb++;
     const TcJob& J = jobs.job[jb];
@@ -232,12 +247,12 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
     const uint32_t bar0 = sbase + (uint32_t)L::BARS;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::SLOT);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    int* issued_slot = reinterpret_cast<int*>(tmem_slot + 2);  // tasks whose copies the gather warps issued
+    int* issued_slot = reinterpret_cast<int*>(tmem_slot + 2);  // stages whose copies the producers issued
     uint4* sdesc = reinterpret_cast<uint4*>(smem + L::DESC);
     uint16_t* scol = reinterpret_cast<uint16_t*>(smem + L::DESC + 16 * (size_t)cap);
     // FULL: the coefficient rows (one arrival per copying thread, when its
     // cp.async copies have landed) and the tile slices (bytes of the bulk
-    // copies, added to the barrier's transaction count) of a stage
+    // copies, added to the barrier's transaction count) of a stage's tasks
     auto FULL = [&](int s) { return bar0 + 8u * s; };
     auto EMPTY = [&](int s) { return bar0 + 8u * (NS + s); };  // MMAs done with the stage
     auto ACCF = [&](int b) { return bar0 + 8u * (2 * NS + b); };
@@ -247,7 +262,7 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const HistChunk ch = J.chunks[cta];
     // failure test (stall_task >= 0): the first CTA withholds the copies and
-    // arrivals of its task stall_task, and every wait of that CTA gives up
+    // arrivals of its stage stall_task, and every wait of that CTA gives up
     // after stall_bound ns, so the launch ends through the abort path
     const bool stall_cta = stall_task >= 0 && blockIdx.x == 0;
     const unsigned long long bound = stall_cta ? stall_bound : WAIT_NS;
@@ -255,8 +270,9 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
 
     // the chunk's task list and the row block's column order, staged once
     for (int i = tid; i < ntask; i += TC_THREADS) sdesc[i] = tasks[ch.first + i];
-    if (!BULK)
+    if (L::SCOL)
         for (int p = tid; p < npad; p += TC_THREADS) scol[p] = (uint16_t)colidx[(size_t)ch.rb * npad + p];
+    const int* __restrict__ gcol = colidx + (size_t)ch.rb * npad;  // the same order in global memory
     if (tid == 0) {
         for (int s = 0; s < NS; s++) {
             mbar_init(FULL(s), BULK ? 1 : NPROD);
@@ -285,19 +301,25 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
         if (tid == 0) {
             const int slot_i = (int)(step_i % R);
             const size_t pslice = (size_t)npad * 128;  // elements of one slice of one ring part (all blocks)
-            int issued = 0;
+            int v = 0;  // tasks that take part (lag within the march so far)
+            int s = 0;
             for (int ti = 0; ti < ntask; ti++) {
                 const uint4 d = sdesc[ti];
                 const int cb = pk_cb(d), k = pk_k(d), code = pk_code(d);
                 if (step_i - k < 1) continue;
-                const int j = issued;
-                const int s = j % NS;
-                if (!mbar_wait(EMPTY(s), ((uint32_t)(j / NS) & 1u) ^ 1u, abort_flag, err, 2, bound)) break;
-                issued = j + 1;
-                *issued_slot = issued;
+                const int j = v / TP, u = v % TP;
+                s = j % NS;
+                v++;
+                if (u == 0) {
+                    if (!mbar_wait(EMPTY(s), ((uint32_t)(j / NS) & 1u) ^ 1u, abort_flag, err, 2, bound)) {
+                        v = -1;
+                        break;
+                    }
+                    *issued_slot = j + 1;
+                }
                 if (stall_cta && j == stall_task) continue;  // failure test: this stage is never filled
-                mbar_expect_tx(FULL(s), STAGE);  // the one arrival, with every byte of the stage
-                const uint32_t adst = sbase + s * STAGE;
+                mbar_add_tx(FULL(s), STAGE);  // every byte of the task, before the stage's one arrival
+                const uint32_t adst = sbase + s * SSTAGE + u * STAGE;
 #pragma unroll
                 for (int q = 0; q < 3; q++) {
                     bulk_g2s(adst + STAGE_A + (2 * q) * B_SLICE, tiles16 + ((size_t)d.x * 3 + q) * (T * T), B_SLICE,
@@ -320,7 +342,10 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
 #pragma unroll
                     for (int q = 0; q < 3; q++) bulk_g2s(adst + q * A_SLICE, blk + q * pslice, A_SLICE, FULL(s));
                 }
+                if (u == TP - 1) mbar_arrive(FULL(s));  // the stage is complete
             }
+            // a last stage with fewer than TP tasks
+            if (v > 0 && v % TP != 0 && !(stall_cta && (v - 1) / TP == stall_task)) mbar_arrive(FULL(s));
         }
     } else if (!BULK && warp < 2) {
         // ---------------- gather: coefficient rows and the tile copy ----------------
@@ -334,8 +359,6 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
         for (int ro = 0; ro < 4; ro++)
 #pragma unroll
             for (int h = 0; h < 2; h++) dofs[ro][h] = a_chunk(ro * 8 + l8, (2 * warp + h) * 4 + l3);
-        int issued = 0;  // tasks whose copies were issued
-        bool ok = true;
         const size_t pstride = (size_t)npad * C2;  // elements of one bf16 slice of one panel
         // 16-byte pieces per coefficient row (C2 / 8); a batch below 64 waves
         // leaves the panel's upper columns uncopied (their TMEM lanes are never
@@ -352,39 +375,42 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
             soff0[h] = mg * 8;
             soff1[h] = sw * 8;
         }
+        int v = 0;  // tasks that take part
+        int s = 0;
         for (int ti = 0; ti < ntask; ti++) {
             const uint4 d = sdesc[ti];
             const int cb = pk_cb(d), k = pk_k(d), code = pk_code(d);
             if (step_i - k < 1) continue;
-            const int j = issued;
-            const int s = j % NS;
-            if (!mbar_wait(EMPTY(s), ((uint32_t)(j / NS) & 1u) ^ 1u, abort_flag, err, 2, bound)) {
-                ok = false;
-                break;
+            const int j = v / TP, u = v % TP;
+            s = j % NS;
+            v++;
+            if (u == 0) {
+                if (!mbar_wait(EMPTY(s), ((uint32_t)(j / NS) & 1u) ^ 1u, abort_flag, err, 2, bound)) {
+                    v = -1;
+                    break;
+                }
+                if (t == 0) *issued_slot = j + 1;
             }
-            if (stall_cta && j == stall_task) {  // failure test: this stage is never filled
-                issued = j + 1;
-                if (t == 0) *issued_slot = issued;
-                continue;
-            }
+            if (stall_cta && j == stall_task) continue;  // failure test: this stage is never filled
+            const uint32_t adst = sbase + s * SSTAGE + u * STAGE;
             if (t == 0) {  // slices in the order Y0 Z0 Y1 Z1 Y2 Z2; bytes added before this thread's arrival
                 mbar_add_tx(FULL(s), STAGE_B);
 #pragma unroll
                 for (int q = 0; q < 3; q++) {
-                    bulk_g2s(sbase + s * STAGE + STAGE_A + (2 * q) * B_SLICE, tiles16 + ((size_t)d.x * 3 + q) * (T * T),
+                    bulk_g2s(adst + STAGE_A + (2 * q) * B_SLICE, tiles16 + ((size_t)d.x * 3 + q) * (T * T), B_SLICE,
+                             FULL(s));
+                    bulk_g2s(adst + STAGE_A + (2 * q + 1) * B_SLICE, tiles16 + ((size_t)d.y * 3 + q) * (T * T),
                              B_SLICE, FULL(s));
-                    bulk_g2s(sbase + s * STAGE + STAGE_A + (2 * q + 1) * B_SLICE,
-                             tiles16 + ((size_t)d.y * 3 + q) * (T * T), B_SLICE, FULL(s));
                 }
             }
             const int part = code & 3, var = (code >> 2) & 3;
             const __nv_bfloat16* pan = part == 2 ? win16 + (size_t)k * 3 * pstride
                                                  : ring16 + (((size_t)(slot_i - k + (slot_i < k ? R : 0)) * 2 + part) * 3) * pstride;
             const int swap = (part != 2 && var == 2) ? 1 : 0;  // [-v, u]: the u and v halves exchanged
-            const uint32_t adst = sbase + s * STAGE;
 #pragma unroll
             for (int ro = 0; ro < 4; ro++) {
-                const __nv_bfloat16* row = pan + (size_t)scol[cb * T + ro * 8 + l8] * C2;
+                const int c = cb * T + ro * 8 + l8;
+                const __nv_bfloat16* row = pan + (size_t)(L::SCOL ? (int)scol[c] : __ldg(gcol + c)) * C2;
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
                     if (!has[h]) continue;
@@ -394,16 +420,15 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
                 }
             }
             // this thread's arrival on the stage fires when its copies have landed
-            cp_async_arrive_noinc(FULL(s));
-            issued = j + 1;
-            if (t == 0) *issued_slot = issued;
+            if (u == TP - 1) cp_async_arrive_noinc(FULL(s));
         }
-        (void)ok;
+        // a last stage with fewer than TP tasks
+        if (v > 0 && v % TP != 0 && !(stall_cta && (v - 1) / TP == stall_task)) cp_async_arrive_noinc(FULL(s));
         cp_async_wait_all();  // this thread's row copies have landed
     } else if (warp == 2) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            int j = 0, g = -1, ing = 0, cur = -1;
+            int v = 0, g = -1, ing = 0, cur = -1, s = 0;
             uint32_t dcol = 0;
             for (int ti = 0; ti < ntask; ti++) {
                 const uint4 d = sdesc[ti];
@@ -419,11 +444,14 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
                     tc_fence_after();
                     dcol = tmem + (uint32_t)(b * BUFCOLS);
                 }
-                const int s = j % NS;
-                if (!mbar_wait(FULL(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 4, bound)) break;
-                if (!BULK) fence_proxy_async();  // coefficient rows written by cp.async (generic proxy)
-                tc_fence_after();
-                const uint32_t a0 = sbase + s * STAGE, b0 = a0 + STAGE_A;
+                const int j = v / TP, u = v % TP;
+                s = j % NS;
+                if (u == 0) {
+                    if (!mbar_wait(FULL(s), (uint32_t)(j / NS) & 1u, abort_flag, err, 4, bound)) break;
+                    if (!BULK) fence_proxy_async();  // coefficient rows written by cp.async (generic proxy)
+                    tc_fence_after();
+                }
+                const uint32_t a0 = sbase + s * SSTAGE + u * STAGE, b0 = a0 + STAGE_A;
                 // K-half kk: A rows 16 kk .. 16 kk + 15 (two 1 KB row groups),
                 // B columns 16 kk .. (32 bytes into each 64-byte row)
 #pragma unroll
@@ -433,10 +461,11 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
                     mma_bf16(dcol + 64, desc_a_sw128(a0 + A_SLICE + kk * 2048), bd, idesc_bf16(128), 1u);
                     mma_bf16(dcol + 128, desc_a_sw128(a0 + 2 * A_SLICE + kk * 2048), bd, idesc_bf16(64), 1u);
                 }
-                tc_commit(EMPTY(s));
+                if (u == TP - 1) tc_commit(EMPTY(s));  // the stage's tasks are done with its buffers
                 ing++;
-                j++;
+                v++;
             }
+            if (v % TP != 0) tc_commit(EMPTY(s));  // a last stage with fewer than TP tasks
             // the last (or interrupted) group: its commit also tells the
             // epilogue that every MMA issued by this thread has completed
             if (g >= 0) tc_commit(ACCF(g % NB));
@@ -453,11 +482,11 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
         // outputs this warp folds: both (EW = 4), or one (EW = 8: warps 3-6 s1, 7-10 s2)
         constexpr int NO = EW == 8 ? 1 : 2;
         const int o0 = EW == 8 ? (warp - 3) >> 2 : 0;
-        float hs[NO][32], hc[NO][32];  // compensated sums
+        float2 hs[NO][16], hc[NO][16];  // compensated sums, tile rows 2n and 2n + 1 in a pair
 #pragma unroll
         for (int o = 0; o < NO; o++)
 #pragma unroll
-            for (int n = 0; n < 32; n++) hs[o][n] = hc[o][n] = 0.f;
+            for (int n = 0; n < 16; n++) hs[o][n] = hc[o][n] = make_float2(0.f, 0.f);
         // per-column scale of each coefficient transform. Gathered form: panel
         // column m is u of wave m (m < B) or v of wave m - B. Bulk form: u of
         // wave m & 63 in the first half (m < 64), v in the second.
@@ -470,6 +499,7 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
         // releases it (one arrival per epilogue warp)
         auto fold = [&](uint32_t col, float c, int o, bool release, int b) {
             float va[32], vb[32];
+            const float2 cc = make_float2(c, c);
             if constexpr (EW == 8) {
                 // one output per warp: the three blocks in one round trip of
                 // TMEM loads, then the buffer is released before the arithmetic
@@ -484,15 +514,17 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
                     if (lane == 0) mbar_arrive(ACCE(b));
                 }
 #pragma unroll
-                for (int n = 0; n < 32; n++) hc[o][n] += c * (va[n] + vb[n]);
+                for (int n = 0; n < 16; n++)
+                    hc[o][n] = f2fma(cc, pair_of(vb, n), f2fma(cc, pair_of(va, n), hc[o][n]));
 #pragma unroll
-                for (int n = 0; n < 32; n++) two_sum(hs[o][n], hc[o][n], c * vl[n]);
+                for (int n = 0; n < 16; n++) two_sum2(hs[o][n], hc[o][n], f2mul(cc, pair_of(vl, n)));
             } else {
                 tmem_ld32(col + 64, va);   // terms of relative size 2^-8
                 tmem_ld32(col + 128, vb);  // and 2^-16
                 tmem_wait_ld();
 #pragma unroll
-                for (int n = 0; n < 32; n++) hc[o][n] += c * (va[n] + vb[n]);
+                for (int n = 0; n < 16; n++)
+                    hc[o][n] = f2fma(cc, pair_of(vb, n), f2fma(cc, pair_of(va, n), hc[o][n]));
                 tmem_ld32(col, va);  // the leading products
                 tmem_wait_ld();
                 if (release) {
@@ -501,7 +533,7 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
                     if (lane == 0) mbar_arrive(ACCE(b));
                 }
 #pragma unroll
-                for (int n = 0; n < 32; n++) two_sum(hs[o][n], hc[o][n], c * va[n]);
+                for (int n = 0; n < 16; n++) two_sum2(hs[o][n], hc[o][n], f2mul(cc, pair_of(va, n)));
             }
         };
         auto drain = [&](int gg, int key) -> bool {
@@ -538,7 +570,10 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
             for (int o = 0; o < NO; o++) {
                 double* p = partial + ((size_t)cta * 2 + o0 + o) * T * C2 + ocol;
 #pragma unroll
-                for (int n = 0; n < 32; n++) p[(size_t)n * C2] = (double)hs[o][n] + (double)hc[o][n];
+                for (int n = 0; n < 16; n++) {
+                    p[(size_t)(2 * n) * C2] = (double)hs[o][n].x + (double)hc[o][n].x;
+                    p[(size_t)(2 * n + 1) * C2] = (double)hs[o][n].y + (double)hc[o][n].y;
+                }
             }
         }
     }
@@ -550,8 +585,8 @@ __global__ void __launch_bounds__(tc_threads<EW>(), 1)
     }
     // After an abort (every role has stopped: the flag is final here), tile
     // copies of stages the MMA thread never consumed may still be in flight:
-    // wait (bounded) for the stages of the last NS issued tasks before the
-    // CTA's shared memory is released.
+    // wait (bounded) for the last NS issued stages before the CTA's shared
+    // memory is released.
     if (tid == 0 && *abort_flag) {
         const int issued = *issued_slot;
         for (int jj = issued > NS ? issued - NS : 0; jj < issued; jj++)
@@ -688,20 +723,30 @@ size_t history_tc_ring_slot_elems(const mot_handle* h) {
 }
 
 
-// pipeline depth: the deepest that fits with `cap` staged tasks (and the row
-// block's column order in the gathered form)
-int history_tc_stages(int npad, bool bulk, int cap) {
-    if (npad > 65536) return 0;
-    const size_t mx = TC_SMEM_MAX;
-    if (bulk) {
-        if (TcLayout<6, true>::bytes(npad, cap) <= mx) return 6;
-        if (TcLayout<5, true>::bytes(npad, cap) <= mx) return 5;
-        return TcLayout<4, true>::bytes(npad, cap) <= mx ? 4 : 0;
+// Pipeline configurations of the history kernel: (stages, tasks per stage).
+// Whether one fits in shared memory with `cap` staged tasks (and, for the
+// gathered form with one task per stage, the row block's column order).
+bool history_tc_config_fits(int npad, bool bulk, int cap, int ns, int tp) {
+    if (npad > 65536) return false;
+    size_t b = 0;
+    if (tp == 1) {
+        if (ns == 4) b = bulk ? TcLayout<4, true, 1>::bytes(npad, cap) : TcLayout<4, false, 1>::bytes(npad, cap);
+        else if (ns == 5) b = bulk ? TcLayout<5, true, 1>::bytes(npad, cap) : TcLayout<5, false, 1>::bytes(npad, cap);
+        else return false;
+    } else if (tp == 2) {
+        if (ns == 2) b = bulk ? TcLayout<2, true, 2>::bytes(npad, cap) : TcLayout<2, false, 2>::bytes(npad, cap);
+        else if (ns == 3) b = bulk ? TcLayout<3, true, 2>::bytes(npad, cap) : TcLayout<3, false, 2>::bytes(npad, cap);
+        else return false;
+    } else {
+        return false;
     }
-    if (TcLayout<6, false>::bytes(npad, cap) <= mx) return 6;
-    if (TcLayout<5, false>::bytes(npad, cap) <= mx) return 5;
-    if (TcLayout<4, false>::bytes(npad, cap) <= mx) return 4;
-    return 0;
+    return b <= TC_SMEM_MAX;
+}
+
+// the default configuration: the deepest one-task pipeline that fits
+int history_tc_stages(int npad, bool bulk, int cap) {
+    if (history_tc_config_fits(npad, bulk, cap, 5, 1)) return 5;
+    return history_tc_config_fits(npad, bulk, cap, 4, 1) ? 4 : 0;
 }
 
 bool history_tc_fits(int npad, bool bulk) { return history_tc_stages(npad, bulk, MOT_TC_CHUNK) > 0; }
@@ -744,39 +789,45 @@ void launch_jobs(mot_handle* h0, TcJobs& jobs, int nctas, int max_npad, int cap,
     static std::atomic<unsigned long long> attr{0};
     once_per_device(attr, h0->dev, [] {
         const int mx = (int)TC_SMEM_MAX;
-        cudaFuncSetAttribute(k_hist_tc<6, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<5, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<4, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<6, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<5, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<4, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<6, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<5, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<4, false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<6, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<5, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        cudaFuncSetAttribute(k_hist_tc<4, true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+#define MOT_TC_ATTR(NSV, BV, EWV, TPV) \
+    cudaFuncSetAttribute(k_hist_tc<NSV, BV, EWV, TPV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)
+#define MOT_TC_ATTR_ALL(BV, EWV) \
+    MOT_TC_ATTR(4, BV, EWV, 1);  \
+    MOT_TC_ATTR(5, BV, EWV, 1);  \
+    MOT_TC_ATTR(2, BV, EWV, 2);  \
+    MOT_TC_ATTR(3, BV, EWV, 2)
+        MOT_TC_ATTR_ALL(false, 4);
+        MOT_TC_ATTR_ALL(false, 8);
+        MOT_TC_ATTR_ALL(true, 4);
+        MOT_TC_ATTR_ALL(true, 8);
+#undef MOT_TC_ATTR_ALL
+#undef MOT_TC_ATTR
     });
     // failure test of the bounded waits (mot_options.hist_stall_test), off by default
     const int stall = h0->opt.hist_stall_test > 0 ? h0->opt.hist_stall_test - 1 : -1;
-    const int deepest = mot::history_tc_stages(max_npad, h0->tc_bulk, cap);
-    const int ns = h0->tc_stages > 0 ? std::min(h0->tc_stages, deepest) : deepest;
-    const bool e8 = h0->tc_epi == 8;
-#define MOT_TC_LAUNCH(NSV, BV, EWV)                                                                            \
-    k_hist_tc<NSV, BV, EWV><<<nctas, tc_threads<EWV>(), TcLayout<NSV, BV>::bytes(max_npad, cap), s>>>( \
-        jobs, cap, stall, 1000000ull)
-#define MOT_TC_LAUNCH_NS(BV, EWV)              \
-    if (ns == 6) MOT_TC_LAUNCH(6, BV, EWV);    \
-    else if (ns == 5) MOT_TC_LAUNCH(5, BV, EWV); \
-    else MOT_TC_LAUNCH(4, BV, EWV)
-    if (h0->tc_bulk) {
-        if (e8) MOT_TC_LAUNCH_NS(true, 8);
-        else MOT_TC_LAUNCH_NS(true, 4);
-    } else {
-        if (e8) MOT_TC_LAUNCH_NS(false, 8);
-        else MOT_TC_LAUNCH_NS(false, 4);
+    // the handles' tuned configuration if it fits, else the deepest one-task pipeline
+    int ns = h0->tc_stages, tp = h0->tc_tps;
+    if (ns <= 0 || !history_tc_config_fits(max_npad, h0->tc_bulk, cap, ns, tp)) {
+        ns = history_tc_stages(max_npad, h0->tc_bulk, cap);
+        tp = 1;
     }
-#undef MOT_TC_LAUNCH_NS
+    const bool e8 = h0->tc_epi == 8;
+#define MOT_TC_LAUNCH(NSV, BV, EWV, TPV)                                                                         \
+    k_hist_tc<NSV, BV, EWV, TPV><<<nctas, tc_threads<EWV>(), TcLayout<NSV, BV, TPV>::bytes(max_npad, cap), s>>>( \
+        jobs, cap, stall, 1000000ull)
+#define MOT_TC_LAUNCH_CFG(BV, EWV)                        \
+    if (tp == 2 && ns == 3) MOT_TC_LAUNCH(3, BV, EWV, 2); \
+    else if (tp == 2) MOT_TC_LAUNCH(2, BV, EWV, 2);       \
+    else if (ns == 5) MOT_TC_LAUNCH(5, BV, EWV, 1);       \
+    else MOT_TC_LAUNCH(4, BV, EWV, 1)
+    if (h0->tc_bulk) {
+        if (e8) MOT_TC_LAUNCH_CFG(true, 8);
+        else MOT_TC_LAUNCH_CFG(true, 4);
+    } else {
+        if (e8) MOT_TC_LAUNCH_CFG(false, 8);
+        else MOT_TC_LAUNCH_CFG(false, 4);
+    }
+#undef MOT_TC_LAUNCH_CFG
 #undef MOT_TC_LAUNCH
     h0->launches++;
 }

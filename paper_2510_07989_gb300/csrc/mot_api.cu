@@ -1659,8 +1659,9 @@ int fit_partial(mot_handle* h) {
 
 // Autotuner of the tensor-core history for handles marched together (one
 // launch serves all of them): every candidate (tasks per chunk, lags per L2
-// range, pipeline depth) is applied, launched once to warm up and three times
-// timed with CUDA events on s; the fastest (median) is kept. The launches
+// range, pipeline stages and tasks per stage, epilogue warps) is applied,
+// launched once to warm up and three times timed with CUDA events on s; the
+// fastest (median) is kept. The launches
 // read the current march state and write only the chunk sums and the history
 // sums of the work area, which every step recomputes before use.
 int tune_tc(mot_handle* const* hs, int n, cudaStream_t s) {
@@ -1674,7 +1675,7 @@ int tune_tc(mot_handle* const* hs, int n, cudaStream_t s) {
     }
     const bool bulk = hs[0]->tc_bulk;
     float best = 1e30f;
-    int bcap = MOT_TC_CHUNK, bns = 0, bepi = 4;
+    int bcap = MOT_TC_CHUNK, bns = 0, bepi = 4, btp = 1;
     double blf = 0.4;
     const int caps[] = {256, 512, 1024};
     const double fracs[] = {0.2, 0.4, 0.8};
@@ -1688,11 +1689,14 @@ int tune_tc(mot_handle* const* hs, int n, cudaStream_t s) {
             }
             int listcap = 1;
             for (int k = 0; k < n; k++) listcap = std::max(listcap, hs[k]->hist_tc_list.cap);
-            for (int ns = 4; ns <= 6; ns++)
+            const int cfgs[][2] = {{4, 1}, {5, 1}, {2, 2}, {3, 2}};  // (stages, tasks per stage)
+            for (const auto& cf : cfgs)
                 for (int epi = 4; epi <= 8; epi += 4) {
-                    if (ns > history_tc_stages(max_npad, bulk, listcap)) continue;
+                    const int ns = cf[0], tp = cf[1];
+                    if (!history_tc_config_fits(max_npad, bulk, listcap, ns, tp)) continue;
                     for (int k = 0; k < n; k++) {
                         hs[k]->tc_stages = ns;
+                        hs[k]->tc_tps = tp;
                         hs[k]->tc_epi = epi;
                     }
                     launch_history_tc_many(hs, n, s1.data(), s2.data(), s, false);
@@ -1706,6 +1710,7 @@ int tune_tc(mot_handle* const* hs, int n, cudaStream_t s) {
                         bcap = cap;
                         blf = lf;
                         bns = ns;
+                        btp = tp;
                         bepi = epi;
                     }
                 }
@@ -1715,6 +1720,7 @@ int tune_tc(mot_handle* const* hs, int n, cudaStream_t s) {
         if ((st = make_tc_list(hs[k], hs[k]->tc_tasks_host, hs[k]->tc_rbs_host, bcap, blf)) != MOT_OK) return st;
         if ((st = fit_partial(hs[k])) != MOT_OK) return st;
         hs[k]->tc_stages = bns;
+        hs[k]->tc_tps = btp;
         hs[k]->tc_epi = bepi;
         hs[k]->tc_tuned = true;
         hs[k]->tc_tune_ms = best;
@@ -1739,6 +1745,29 @@ MOT_API int mot_tune(mot_handle* const* hs, int n, void* stream) {
     }
     CK_H(hs[0], cudaSetDevice(hs[0]->dev));
     return tune_tc(hs, n, (cudaStream_t)stream);
+}
+
+MOT_API int mot_set_tc_config(mot_handle* h, int cap, double lag_frac, int stages, int tasks_per_stage,
+                              int epilogue_warps) {
+    if (!h) return MOT_EINVAL;
+    if (!h->hist_tc || h->step < 1)
+        return fail(h, MOT_ESTATE, "mot_set_tc_config: needs a handle on the tensor-core history that has taken a step");
+    if (cap < 1 || cap > MOT_TC_CHUNK || !(lag_frac > 0.0 && lag_frac <= 1.0) ||
+        (epilogue_warps != 4 && epilogue_warps != 8))
+        return fail(h, MOT_EINVAL, "mot_set_tc_config: configuration out of range");
+    CK_H(h, cudaSetDevice(h->dev));
+    int st;
+    if ((st = make_tc_list(h, h->tc_tasks_host, h->tc_rbs_host, cap, lag_frac)) != MOT_OK) return st;
+    if (!h->hist_tc_list.packed) return fail(h, MOT_EINVAL, "tensor-core list not available");
+    if (!history_tc_config_fits(h->npad, h->tc_bulk, h->hist_tc_list.cap, stages, tasks_per_stage))
+        return fail(h, MOT_EINVAL, "mot_set_tc_config: stages x tasks per stage do not fit in shared memory");
+    if ((st = fit_partial(h)) != MOT_OK) return st;
+    h->tc_stages = stages;
+    h->tc_tps = tasks_per_stage;
+    h->tc_epi = epilogue_warps;
+    h->tc_tuned = false;
+    h->tc_tune_ms = 0;
+    return MOT_OK;
 }
 
 MOT_API int mot_run_many(mot_handle* const* hs, int n, int n_steps, const mot_wave* const* waves, const int* B,
@@ -2078,6 +2107,7 @@ MOT_API int mot_get_info(mot_handle* h, mot_info* info) {
     info->tc_lag_frac = h->tc_lag_frac;
     info->tc_stages = h->tc_stages;
     info->tc_epilogue_warps = h->tc_epi;
+    info->tc_tasks_per_stage = h->tc_tps;
     info->tc_tuned = h->tc_tuned ? 1 : 0;
     info->tc_tune_ms = h->tc_tune_ms;
     info->tc_launches = h->tc_launches;

@@ -173,6 +173,7 @@ struct mot_handle {
     int tc_stages = 0;             // pipeline depth of the tensor-core history (0: the deepest that fits)
     int tc_cap = 0;                // tasks per chunk the tensor-core list was cut with
     int tc_epi = 4;                // epilogue warps of the tensor-core history (4 or 8)
+    int tc_tps = 1;                // tasks per pipeline stage of the tensor-core history (1 or 2)
     double tc_lag_frac = 0;        // fraction of L2 a lag range of the list may fill
     bool tc_tuned = false;         // the three were chosen by mot_tune
     float tc_tune_ms = 0;          // the chosen configuration's launch time in the tuning (ms)
@@ -254,6 +255,8 @@ void launch_split_ring(mot_handle* h, int slot, cudaStream_t s);
 bool history_tc_fits(int npad, bool bulk);  // the kernel's shared memory fits (gathered form: with the column order)
 size_t history_tc_ring_slot_elems(const mot_handle* h);  // bf16 elements of one ring slot of d_ring16
 int history_tc_stages(int npad, bool bulk, int cap);
+// whether (ns stages of tp tasks) fits the kernel's shared memory with cap staged tasks
+bool history_tc_config_fits(int npad, bool bulk, int cap, int ns, int tp);
 float launch_history_tc_many(mot_handle* const* hs, int n, double* const* s1, double* const* s2, cudaStream_t s,
                              bool timed);
 

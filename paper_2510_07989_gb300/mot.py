@@ -70,7 +70,7 @@ class mot_info(ctypes.Structure):
                 ("gmres_iters_total", ctypes.c_int64), ("tc_chunk_cap", ctypes.c_int32),
                 ("tc_lag_frac", ctypes.c_double), ("tc_stages", ctypes.c_int32), ("tc_tuned", ctypes.c_int32),
                 ("tc_tune_ms", ctypes.c_double), ("tc_launches", ctypes.c_int64),
-                ("tc_epilogue_warps", ctypes.c_int32)]
+                ("tc_epilogue_warps", ctypes.c_int32), ("tc_tasks_per_stage", ctypes.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,7 +79,7 @@ class mot_info(ctypes.Structure):
 
 
 EXPORTED = ["mot_create", "mot_load_operators", "mot_set_frequencies", "mot_step", "mot_run", "mot_run_many",
-            "mot_tune", "mot_get_currents",
+            "mot_tune", "mot_set_tc_config", "mot_get_currents",
             "mot_fields", "mot_fields_noalloc", "mot_reset", "mot_save_state", "mot_load_state", "mot_get_info",
             "mot_get_edges", "mot_last_error", "mot_destroy"]
 
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH):
     lib.mot_run.argtypes = [vp, i32, vp, i32, vp, vp]
     lib.mot_run_many.argtypes = [vp, i32, i32, vp, vp, vp, vp]
     lib.mot_tune.argtypes = [vp, i32, vp]
+    lib.mot_set_tc_config.argtypes = [vp, i32, dbl, i32, i32, i32]
     lib.mot_get_currents.argtypes = [vp, vp]
     lib.mot_fields.argtypes = [vp, vp, i32, vp, vp]
     lib.mot_fields_noalloc.argtypes = [vp, vp, i32, vp, vp]
@@ -278,6 +279,13 @@ def mot_tune(handles, stream=None) -> None:
     lib = load_library()
     hs = (ctypes.c_void_p * max(n, 1))(*[h.ptr for h in handles])
     _check(handles[0].ptr if n else None, lib.mot_tune(hs, n, _stream(stream)))
+
+
+def mot_set_tc_config(h: Handle, cap: int, lag_frac: float, stages: int, tasks_per_stage: int,
+                      epilogue_warps: int) -> None:
+    """mot_set_tc_config: apply one tensor-core history configuration as given."""
+    _check(h.ptr, load_library().mot_set_tc_config(h.ptr, int(cap), float(lag_frac), int(stages),
+                                                   int(tasks_per_stage), int(epilogue_warps)))
 
 
 def mot_get_currents(h: Handle, out) -> None:

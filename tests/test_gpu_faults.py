@@ -56,10 +56,12 @@ def test_cg_iteration_limit_flags_and_continues(M, pr1_ops):
     assert "CG" in M.mot_last_error(s.h)
 
 
-def test_history_wait_bound_ends_in_error_status(M):
+@pytest.mark.parametrize("tasks_per_stage", [1, 2])
+def test_history_wait_bound_ends_in_error_status(M, tasks_per_stage):
     """The device side of failure detection, in the allowed form: with
     hist_stall_test the first CTA of every tensor-core history launch withholds
-    one stage's copies and arrivals (a barrier phase nothing completes) and its
+    one stage's copies and arrivals (a barrier phase nothing completes; stages
+    of one task, and of two tasks behind one barrier pair) and its
     waits give up after 1 ms. The CTA takes its abort path (stops issuing,
     drains the copies in flight, releases TMEM, raises the error word) and
     mot_step returns MOT_ECUDA; the context stays usable: a fresh handle then
@@ -70,6 +72,9 @@ def test_history_wait_bound_ends_in_error_status(M):
     exc = MS.fibonacci_batch(64, ops.dt, w_steps=30, t0_steps=60)
     waves = M.mot_waves(exc)
     s = M.Solver(ops, precision=M.MOT_PREC_MIXED, hist_stall_test=4)
+    M.mot_step(s.h, waves, 64)  # step 1 has no history (every lag >= 1): nothing stalls
+    if tasks_per_stage == 2:  # two tasks behind each barrier pair
+        M.mot_set_tc_config(s.h, 512, 0.4, 2, 2, 4)
     with pytest.raises(M.MotError) as e:
         for _ in range(ops.kmax + 8):
             M.mot_step(s.h, waves, 64)

@@ -149,12 +149,49 @@ def test_tune_keeps_the_march(M, torus_small):
         M.mot_step(s.h, waves, 64, out)
         W[i] = out
     info = s.info()
-    assert info["tc_tuned"] == 1 and info["tc_chunk_cap"] in (256, 512, 1024) and info["tc_stages"] in (4, 5, 6)
+    assert info["tc_tuned"] == 1 and info["tc_chunk_cap"] in (256, 512, 1024) and info["tc_stages"] in (2, 3, 4, 5) and info["tc_tasks_per_stage"] in (1, 2)
     assert info["tc_epilogue_warps"] in (4, 8) and info["tc_tune_ms"] > 0
     errs = [rel(W[:, b].reshape(n, -1), O.march(S, exc, n, b=b)) for b in (0, 63)]
-    print(f"tuned march (cap {info['tc_chunk_cap']}, lag fraction {info['tc_lag_frac']}, {info['tc_stages']} stages, "
+    print(f"tuned march (cap {info['tc_chunk_cap']}, lag fraction {info['tc_lag_frac']}, {info['tc_stages']} stages of {info['tc_tasks_per_stage']}, "
           f"{info['tc_epilogue_warps']} epilogue warps): rel errs", ["%.3e" % e for e in errs])
     assert max(errs) < TOL_MIXED
+
+
+@pytest.mark.parametrize("bulk", [False, True])
+def test_pipeline_configurations_agree(M, torus_small, bulk):
+    """Every pipeline of the tensor-core history -- 4 or 5 stages of one task,
+    2 or 3 stages of two tasks behind one barrier pair, 4 or 8 epilogue warps
+    -- runs the same MMAs and folds in the same order for one chunking, so the
+    marches agree to rounding (bitwise where the rest of the step is
+    deterministic); the first one meets the oracle. Set after step 1 with
+    mot_set_tc_config, gathered and bulk form, torus 12 x 6, B = 64."""
+    ops, S = torus_small
+    exc = MS.fibonacci_batch(64, ops.dt, w_steps=30, t0_steps=60)
+    waves = M.mot_waves(exc)
+    n = 130
+    flags = M.MOT_MIX_DEFAULT | (M.MOT_MIX_TCBULK if bulk else 0)
+    runs = {}
+    for cfg in [(4, 1, 4), (5, 1, 8), (2, 2, 4), (2, 2, 8), (3, 2, 4)]:
+        s = M.Solver(ops, precision=M.MOT_PREC_MIXED, mixed_flags=flags)
+        out = np.zeros((64, 2, ops.ne))
+        W = np.zeros((n, 64, 2, ops.ne))
+        for i in range(n):
+            if i == 1:
+                M.mot_set_tc_config(s.h, 512, 0.4, *cfg)
+            M.mot_step(s.h, waves, 64, out)
+            W[i] = out
+        info = s.info()
+        assert info["hist_kernel"] == 2 and info["tc_tuned"] == 0
+        assert (info["tc_stages"], info["tc_tasks_per_stage"], info["tc_epilogue_warps"]) == cfg
+        runs[cfg] = W.reshape(n, 64, -1)
+        del s
+    W0 = runs[(4, 1, 4)]
+    errs = [rel(W0[:, b], O.march(S, exc, n, b=b)) for b in (0, 63)]
+    diffs = {c: float(np.abs(W - W0).max() / np.abs(W0).max()) for c, W in runs.items()}
+    print(f"pipelines ({'bulk' if bulk else 'gathered'} form): oracle rel errs", ["%.3e" % e for e in errs],
+          "; max rel difference to 4 x 1 stages:", {str(c): "%.1e" % d for c, d in diffs.items()})
+    assert max(errs) < TOL_MIXED
+    assert max(diffs.values()) < 1e-12
 
 
 def test_mixed_save_load_state_resumes_exactly(M, torus_small):
