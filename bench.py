@@ -208,7 +208,7 @@ TRAFFIC = {
     # ncu --profile-from-start off --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:k_hist_tc -c 1
     #     python bench.py --steps 2 --warmup 1 --no-cpu-baseline --fp64-steps 0
-    ("k_hist_tc", "torus64x24"): (32052556288 + 466490368, "329b400539ebe4094959123d37e4328d39602c3c"),
+    ("k_hist_tc", "torus64x24"): (44900189440 + 417015296, "dcee7d90171b04be6fe27a79c864af694c7fbf2c"),
 }
 
 

@@ -166,9 +166,10 @@ __device__ __forceinline__ int task_xform(int code) { return (code & 3) == 2 ? 3
 // NS pipeline stages of TP tasks each (one FULL / EMPTY barrier pair per stage).
 template <int NS, bool BULK, int TP>
 struct TcLayout {
-    // the gathered form with one task per stage stages the row block's column
-    // order in shared memory; with two it reads it through L1 (room for stages)
-    static constexpr bool SCOL = !BULK && TP == 1;
+    // the gathered form stages the row block's column order in shared memory,
+    // except with three stages of two tasks (no room left): it then reads it
+    // through L1
+    static constexpr bool SCOL = !BULK && (TP == 1 || NS == 2);
     static constexpr int NBARS = 2 * NS + 2 * NB + 1;  // + one barrier for the final MMA drain
     static constexpr size_t BARS = (size_t)NS * TP * STAGE;
     static constexpr size_t SLOT = BARS + ((8 * NBARS + 15) / 16) * 16;  // TMEM address, abort flag, issued count
