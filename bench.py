@@ -203,12 +203,16 @@ class Clocks:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel and
 # workload, with the SHA-1 of the device code of the kernel source they were
 # taken on (kernel_source_sha: comments and the host launch code excluded): a
-# changed kernel reports null until the counters are taken again.
+# changed kernel reports null until the counters are taken again. The third
+# item is the chunking the tuner chose in that capture (tasks per chunk, lag
+# fraction of L2), reported beside the figure: DRAM reads depend on it.
 TRAFFIC = {
     # ncu --profile-from-start off --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:k_hist_tc -c 1
     #     python bench.py --steps 2 --warmup 1 --no-cpu-baseline --fp64-steps 0
-    ("k_hist_tc", "torus64x24"): (44900189440 + 417015296, "dcee7d90171b04be6fe27a79c864af694c7fbf2c"),
+    ("k_hist_tc", "torus64x24"): (44900189440 + 417015296, "dcee7d90171b04be6fe27a79c864af694c7fbf2c",
+                                  {"chunk_cap": 512, "lag_frac": 0.4, "stages": 3, "tasks_per_stage": 2,
+                                   "epilogue_warps": 4}),
 }
 
 
@@ -231,10 +235,11 @@ def kernel_source_sha(name):
 
 
 def traffic_of(kernel, workload, source):
+    """(bytes per launch, configuration of the capture) or (None, None)."""
     t = TRAFFIC.get((kernel, workload))
     if t and t[1] == kernel_source_sha(source):
-        return t[0]
-    return None
+        return t[0], t[2]
+    return None, None
 
 
 # issued tensor-core work of one history task: two K-halves of
@@ -429,9 +434,10 @@ def roofline_of(info0, info1, ms_step, steps, workload, peaks, how):
         achieved = hbytes / (ms_l / 1e3) / 1e9 if ms_l else None
         tc_flops = info1["hist_tc_tasks"] * TC_FLOPS_PER_TASK
         bf16 = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        traffic, traffic_cfg = traffic_of("k_hist_tc", workload, "k_tc_hist.cu")
         roof = {"kernel": "k_hist_tc", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm if achieved else None,
-                "traffic": traffic_of("k_hist_tc", workload, "k_tc_hist.cu"),
+                "traffic": traffic, "traffic_config": traffic_cfg,
                 "peak_source": f"measured copy bandwidth ({how})",
                 "algorithmic_bytes_per_launch": hbytes, "algorithmic_flops_per_launch": flops,
                 "tensor_issued_tflops": tc_flops / (ms_l / 1e3) / 1e12 if ms_l else None,
