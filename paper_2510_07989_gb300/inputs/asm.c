@@ -1009,6 +1009,9 @@ void asm_td_free(void* h) {
  * triangles t of D(v), so that T_0^h = Lambda S Lambda^T.
  * g_n|_t(x) = alpha x + beta; needs the moments I0, Ix, Iy, Ixy of 1/R over
  * refined triangle pairs.
+ * kappa > 0: the EFIO with the imaginary wavenumber -i kappa in place of the
+ * static one (Section IV-A remark): the kernel 1/R becomes exp(-kappa R)/R
+ * (same normalisations 1/D and D); kappa = 0 is the static operator exactly.
  */
 typedef struct {
     int nref, ne, nv;
@@ -1025,6 +1028,7 @@ typedef struct {
     const int* ctri;
     const int* v_edges_ptr_dummy;
     double D;
+    double kappa;   /* Yukawa decay of the kernel (0: static) */
     int nq;
     Rule1D r1;
     double* half;   /* [2][ne][ne] halves of T_0^s rows */
@@ -1061,6 +1065,7 @@ static void static_moments(const STCtx* C, const Tri* A, const Tri* B, int same,
         double s0 = 0, s1[3] = {0, 0, 0};
         for (int i = 0; i < nn; i++) {
             double v = nodes[i].w / nodes[i].R;
+            if (C->kappa > 0.0) v *= exp(-C->kappa * nodes[i].R);
             s0 += v;
             s1[0] += v * nodes[i].y[0];
             s1[1] += v * nodes[i].y[1];
@@ -1131,11 +1136,13 @@ static void* st_worker(void* arg) {
  * ref_pts: (nref, 3, 3); rvert: dual cell per refined triangle; deg: (nv);
  * bptr/bn/ba/bb: BC entries grouped by refined triangle; cptr/ctri: refined
  * triangles per dual cell; ev: (ne, 2).
+ * kappa: decay of the kernel exp(-kappa R)/R (0: the static 1/R).
  * Outputs T0s (ne x ne, row-major) and S (nv x nv).
  */
 int asm_static(int nref, const double* ref_pts, const int* rvert, int nv, const int* deg, int ne, const int* ev,
                const int64_t* bptr, const int* bn, const double* ba, const double* bb, const int64_t* cptr,
-               const int* ctri, double D, int nq, int ntheta, int nrad, int nthreads, double* T0s, double* S) {
+               const int* ctri, double D, double kappa, int nq, int ntheta, int nrad, int nthreads, double* T0s,
+               double* S) {
     STCtx C;
     memset(&C, 0, sizeof C);
     C.nref = nref;
@@ -1151,6 +1158,7 @@ int asm_static(int nref, const double* ref_pts, const int* rvert, int nv, const 
     C.ctri = ctri;
     C.ev = ev;
     C.D = D;
+    C.kappa = kappa;
     C.nq = nq;
     C.r1.nt = ntheta;
     C.r1.nr = nrad;

@@ -63,8 +63,8 @@ def _load():
         _lib.asm_static.restype = ctypes.c_int
         _lib.asm_static.argtypes = ([ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                      ctypes.c_int, ctypes.c_void_p] + [ctypes.c_void_p] * 6 +
-                                    [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_void_p, ctypes.c_void_p])
+                                    [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p])
     return _lib
 
 
@@ -182,7 +182,11 @@ def _run_medium(mesh: Mesh, c: float, dt: float, tmax: float, kmax: int, nq: int
     return out
 
 
-def _static(mesh: Mesh, dual: DualBasis, D: float, nq: int, ntheta: int, nrad: int, nthreads: int):
+def _static(mesh: Mesh, dual: DualBasis, D: float, nq: int, ntheta: int, nrad: int, nthreads: int,
+            kappa: float = 0.0):
+    """T_0^s and T_0^h of the static EFIO on the BC dual basis (Section IV-A);
+    kappa > 0: those of the EFIO with the imaginary wavenumber -i kappa
+    (kernel exp(-kappa R) / (4 pi R), same normalisation)."""
     lib = _load()
     nref = dual.nref
     order = np.argsort(dual.bc_t, kind="stable")
@@ -205,7 +209,8 @@ def _static(mesh: Mesh, dual: DualBasis, D: float, nq: int, ntheta: int, nrad: i
     T0s = np.zeros((mesh.ne, mesh.ne))
     S = np.zeros((mesh.nv, mesh.nv))
     lib.asm_static(nref, _ptr(pts), _ptr(rvert), mesh.nv, _ptr(deg), mesh.ne, _ptr(ev), _ptr(bptr), _ptr(bn),
-                   _ptr(ba), _ptr(bb), _ptr(cptr), _ptr(ctri), D, nq, ntheta, nrad, nthreads, _ptr(T0s), _ptr(S))
+                   _ptr(ba), _ptr(bb), _ptr(cptr), _ptr(ctri), D, float(kappa), nq, ntheta, nrad, nthreads,
+                   _ptr(T0s), _ptr(S))
     T0s = 0.5 * (T0s + T0s.T)
     S = 0.5 * (S + S.T)
     ne = mesh.ne
@@ -219,13 +224,17 @@ def _static(mesh: Mesh, dual: DualBasis, D: float, nq: int, ntheta: int, nrad: i
 
 def assemble(mesh: Mesh, eps_r: float, mu_r: float, dt: float, *, nq: int = 7, ntheta: int = 4, nrad: int = 4,
              nq_static: int = 3, nthreads: int | None = None, with_bc_table: bool = False,
-             kmax: int | None = None, far_plain: int = 0) -> Operators:
+             kmax: int | None = None, far_plain: int = 0, kappa: float = 0.0) -> Operators:
     """Assemble every input of the MOT step for one scatterer (c = 1 outside).
 
     nq is the outer (test) triangle rule; ntheta / nrad the Gauss orders of the
     polar inner integration per smooth piece. far_plain > 0 replaces the
     shell-split polar rule by a plain far_plain-point triangle rule for source
-    triangles farther than three diameters (fast, less accurate assembly)."""
+    triangles farther than three diameters (fast, less accurate assembly).
+    kappa > 0 builds the Calderon preconditioner from the EFIO T_{-i kappa}
+    (imaginary wavenumber) instead of the static T_0 (Section IV-A remark)."""
+    if kappa < 0:
+        raise ValueError("kappa must be >= 0")
     if nthreads is None:
         nthreads = os.cpu_count() or 1
     c = 1.0
@@ -242,12 +251,13 @@ def assemble(mesh: Mesh, eps_r: float, mu_r: float, dt: float, *, nq: int = 7, n
         for name, m in res.items():
             mats[name + suffix] = m
     dual = dual_basis(mesh)
-    T0s, T0h = _static(mesh, dual, D, nq_static, ntheta, nrad, nthreads)
+    T0s, T0h = _static(mesh, dual, D, nq_static, ntheta, nrad, nthreads, kappa)
     r, cidx, v = gram_matrix(mesh, dual)
     G = sp.coo_matrix((v, (r, cidx)), shape=(mesh.ne, mesh.ne)).tocsr()
     G.sum_duplicates()
     ops = Operators(mesh=mesh, eps_r=eps_r, mu_r=mu_r, dt=dt, c=c, cp=cp, eta=eta, etap=etap, D=D, tmax=tmax,
                     kmax=kmax, mats=mats, T0s=T0s, T0h=T0h, G=G, rwg=rwg_table(mesh, 7), dual=dual,
                     bc=bc_table(dual) if with_bc_table else None,
-                    meta=dict(nq=nq, ntheta=ntheta, nrad=nrad, nq_static=nq_static, far_plain=far_plain))
+                    meta=dict(nq=nq, ntheta=ntheta, nrad=nrad, nq_static=nq_static, far_plain=far_plain,
+                              kappa=kappa))
     return ops

@@ -318,6 +318,56 @@ def cube(side: float = 2.0, n: int = 24) -> Mesh:
     return build_edges(m)
 
 
+def star_pyramid(n_points: int = 5, r_tip: float = 1.0, r_inner: float = 0.4, height: float = 1.0,
+                 m: int = 11) -> Mesh:
+    """Star-based pyramid: a pyramid over a star polygon with n_points tips
+    (the paper's non-smooth third scatterer, Section VI-A, whose exact shape
+    comes from another paper: this is a stand-in with the same character --
+    sharp tips, re-entrant base corners, sharp edges). The base corners c_j
+    (j = 0 .. 2 n_points - 1) sit at angle pi j / n_points, radius r_tip (even
+    j) or r_inner (odd j), in the plane z = 0 around the origin; the apex at
+    (0, 0, height). The surface is 4 n_points flat triangles -- (apex, c_j,
+    c_{j+1}) on the sides, (origin, c_{j+1}, c_j) on the base -- each split
+    uniformly into m^2 triangles (m segments per side), so F = 4 n_points m^2,
+    V = 2 n_points m^2 + 2 (n_points = 5, m = 11: 1212 vertices, 2420
+    triangles, 3630 edges against the paper's 1227, 2450, 3675)."""
+    if n_points < 3 or m < 1 or not (0 < r_inner < r_tip) or height <= 0:
+        raise ValueError("star_pyramid: needs n_points >= 3, m >= 1, 0 < r_inner < r_tip, height > 0")
+    nc = 2 * n_points
+    ang = np.pi * np.arange(nc) / n_points
+    rad = np.where(np.arange(nc) % 2 == 0, r_tip, r_inner)
+    corners = np.stack([rad * np.cos(ang), rad * np.sin(ang), np.zeros(nc)], axis=1)
+    apex = np.array([0.0, 0.0, height])
+    origin = np.zeros(3)
+    big = []
+    for j in range(nc):
+        c0, c1 = corners[j], corners[(j + 1) % nc]
+        big.append((apex, c0, c1))      # side: counter-clockwise seen from outside
+        big.append((origin, c1, c0))    # base: seen from below
+    ids = {}
+    pts = []
+
+    def pid(x):
+        k = tuple(np.round(x, 12))
+        if k not in ids:
+            ids[k] = len(pts)
+            pts.append(x)
+        return ids[k]
+
+    tris = []
+    for A, B, C in big:
+        # grid point (i, j): A + (i / m)(B - A) + (j / m)(C - A), i + j <= m
+        P = [[pid(A + (i / m) * (B - A) + (j / m) * (C - A)) if i + j <= m else -1 for j in range(m + 1)]
+             for i in range(m + 1)]
+        for i in range(m):
+            for j in range(m - i):
+                tris.append((P[i][j], P[i + 1][j], P[i][j + 1]))
+                if i + j + 1 < m:
+                    tris.append((P[i + 1][j], P[i + 1][j + 1], P[i][j + 1]))
+    mesh = Mesh(np.array(pts, dtype=np.float64), np.array(tris, dtype=np.int32), name=f"starpyr{n_points}_{m}")
+    return build_edges(mesh)
+
+
 def diameter(mesh: Mesh) -> float:
     """Scatterer diameter D: the largest vertex-to-vertex distance."""
     v = mesh.verts

@@ -14,6 +14,8 @@ from paper_2510_07989_gb300.inputs.dual import dual_basis, gram_matrix, triangle
     (lambda: MS.torus(1.0, 0.3, 64, 24), (1536, 3072, 4608), 0),
     (lambda: MS.cube(2.0, 24), (3458, 6912, 10368), 2),
     (lambda: MS.geodesic_sphere(5), (252, 500, 750), 2),
+    (lambda: MS.star_pyramid(5, m=11), (1212, 2420, 3630), 2),
+    (lambda: MS.star_pyramid(5, m=2), (42, 80, 120), 2),
 ])
 def test_mesh_counts_euler(make, counts, chi):
     """Counts of the configured workloads; V - E + F = 2 (sphere) or 0 (torus); E = 3F/2."""
@@ -21,6 +23,34 @@ def test_mesh_counts_euler(make, counts, chi):
     assert (m.nv, m.nf, m.ne) == counts
     assert m.nv - m.ne + m.nf == chi
     assert 2 * m.ne == 3 * m.nf
+
+
+@pytest.mark.parametrize("n_points,m", [(5, 2), (5, 11), (3, 4), (7, 3)])
+def test_star_pyramid_geometry(n_points, m):
+    """The star-based pyramid is closed and outward oriented: its signed volume
+    (sum of v0 . (v1 x v2) / 6) equals the analytic n r_tip r_inner
+    sin(pi / n) h / 3 (base of 2n triangles (origin, c_j, c_j+1), cone of
+    height h); its area equals the 4n flat faces' areas from their corners
+    (the uniform split loses nothing); every vertex lies on one of those
+    faces; the base is flat at z = 0 and the apex is the highest point."""
+    r_tip, r_in, h = 1.0, 0.4, 1.0
+    M = MS.star_pyramid(n_points, r_tip, r_in, h, m)
+    v0, v1, v2 = (M.verts[M.tris[:, k]] for k in range(3))
+    vol = np.einsum("ij,ij->i", v0, np.cross(v1, v2)).sum() / 6
+    assert vol == pytest.approx(n_points * r_tip * r_in * np.sin(np.pi / n_points) * h / 3, rel=1e-12)
+    area = 0.5 * np.linalg.norm(np.cross(v1 - v0, v2 - v0), axis=1).sum()
+    nc = 2 * n_points
+    ang = np.pi * np.arange(nc) / n_points
+    rad = np.where(np.arange(nc) % 2 == 0, r_tip, r_in)
+    C = np.stack([rad * np.cos(ang), rad * np.sin(ang), np.zeros(nc)], axis=1)
+    apex = np.array([0.0, 0.0, h])
+    big = 0.0
+    for j in range(nc):
+        c0, c1 = C[j], C[(j + 1) % nc]
+        big += 0.5 * np.linalg.norm(np.cross(c0 - apex, c1 - apex)) + 0.5 * np.linalg.norm(np.cross(c0, c1))
+    assert area == pytest.approx(big, rel=1e-12)
+    assert M.verts[:, 2].min() == pytest.approx(0.0, abs=1e-15) and M.verts[:, 2].max() == pytest.approx(h)
+    assert M.nf == 4 * n_points * m * m and M.nv == 2 * n_points * m * m + 2
 
 
 def test_canonical_edge_rule():
@@ -101,6 +131,73 @@ def test_static_operators_definiteness(pr1_ops):
     assert es[0] > 0
     assert eh[0] > -1e-12 * eh[-1]
     assert int((eh > 1e-10 * eh[-1]).sum()) == ops.mesh.nv - 1
+
+
+@pytest.fixture(scope="module")
+def yukawa_static():
+    """T_0^s, T_0^h of the icosphere L2 (480 edges, D = 2) with the static
+    kernel 1/R and with exp(-kappa R)/R for kappa = 0.5 and 2 (the EFIO with
+    the imaginary wavenumber -i kappa of the Section IV-A remark)."""
+    from paper_2510_07989_gb300.inputs.assemble import _static
+    from paper_2510_07989_gb300.inputs.meshes import diameter
+    m = MS.icosphere(2)
+    dual = dual_basis(m)
+    D = diameter(m)
+    ops = {k: _static(m, dual, D, 3, 4, 4, 8, kappa=k) for k in (0.0, 0.5, 2.0)}
+    return m, ops
+
+
+def test_yukawa_kappa_zero_is_the_static_operator(yukawa_static):
+    """kappa = 0 reproduces the static operators bit for bit."""
+    from paper_2510_07989_gb300.inputs.assemble import _static
+    from paper_2510_07989_gb300.inputs.meshes import diameter
+    m, ops = yukawa_static
+    T0s, T0h = _static(m, dual_basis(m), diameter(m), 3, 4, 4, 8)
+    assert np.array_equal(T0s, ops[0.0][0]) and np.array_equal(T0h, ops[0.0][1])
+
+
+def test_yukawa_operators_definite_and_below_the_static_ones(yukawa_static):
+    """exp(-kappa R)/(4 pi R) is a positive definite kernel (Fourier transform
+    1/(k^2 + kappa^2) > 0), and so is the difference to the static kernel
+    (1/k^2 - 1/(k^2 + kappa^2) > 0): T^s_kappa is SPD and T_0^s - T^s_kappa
+    PSD; T^h_kappa is PSD of rank N_v - 1 and T_0^h - T^h_kappa PSD. The
+    differences are smoothing operators whose small eigenvalues sit at the
+    quadrature error (~2e-5 of their largest for T^s; T^h's dual-cell single
+    layer is exact to rounding here). A kernel with the wrong sign of the
+    exponent makes the differences negative definite."""
+    m, ops = yukawa_static
+    T0s, T0h = ops[0.0]
+
+    def psd(A, rel):
+        e = np.linalg.eigvalsh(A)
+        return e[-1] > 0 and e[0] > -rel * e[-1]
+
+    for kappa in (0.5, 2.0):
+        Ts, Th = ops[kappa]
+        es, eh = np.linalg.eigvalsh(Ts), np.linalg.eigvalsh(Th)
+        assert es[0] > 0
+        assert eh[0] > -1e-12 * eh[-1] and int((eh > 1e-10 * eh[-1]).sum()) == m.nv - 1
+        assert psd(T0s - Ts, 1e-4)
+        assert psd(T0h - Th, 1e-12)
+    # the larger the decay, the smaller the operator
+    assert psd(ops[0.5][0] - ops[2.0][0], 1e-4) and psd(ops[0.5][1] - ops[2.0][1], 1e-12)
+
+
+def test_yukawa_far_pairs_decay_as_the_kernel(yukawa_static):
+    """For BC functions far apart (midpoint distance R > 0.9 D) the
+    interaction is (integral of g_m) . (integral of g_n) times the kernel at
+    R, so T^s_kappa / T_0^s -> exp(-kappa R): within 1 % (median 0.5 %) for
+    kappa = 0.5 on the large entries. exp(-2 kappa R), exp(-kappa R / 4 pi) or
+    exp(+kappa R) miss by 30 % or more."""
+    m, ops = yukawa_static
+    mid = 0.5 * (m.verts[m.ev[:, 0]] + m.verts[m.ev[:, 1]])
+    R = np.linalg.norm(mid[:, None, :] - mid[None, :, :], axis=2)
+    T0, T1 = ops[0.0][0], ops[0.5][0]
+    far = R > 1.8
+    sel = far & (np.abs(T0) > 0.3 * np.abs(T0[far]).max())
+    assert sel.sum() > 1000
+    dev = np.abs(T1[sel] / T0[sel] / np.exp(-0.5 * R[sel]) - 1)
+    assert np.median(dev) < 5e-3 and dev.max() < 1e-2
 
 
 def _lag_sum(mat, kmax_tail=None):
