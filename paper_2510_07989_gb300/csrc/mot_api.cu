@@ -586,6 +586,8 @@ int do_step(mot_handle* h, cudaStream_t s, int phases = STEP_ALL) {
         }
     }
     if ((phases & STEP_HISTORY) && i >= 2) {
+        if (h->hist_tc && !(h->hist_tc_list.packed && h->hist_tc_list.rb_ptr && h->hist_tc_list.rb_chunks))
+            return fail(h, MOT_ESTATE, "tensor-core history: no task list (a re-cut of the list failed)");
         if (h->hist_tc)
             launch_history_tc(h, h->hist_tc_list, i, W.s1, W.s2, s);
         else if (h32)
