@@ -102,6 +102,13 @@ typedef struct {
                               after 1 ms; that CTA stops, drains its copies, releases TMEM
                               and raises the error word, and mot_step returns MOT_ECUDA
                               with the GPU context intact. */
+    int32_t fp64_direct;   /* MOT_PREC_FP64 only. 0 (default): the Gram solves (G^{-1} in the
+                              left factor) by CG on the normal equations and the projector
+                              solves by CG on the graph Laplacians, to cg_tol. 1: by dense
+                              FP64 inverses formed at load (LU with partial pivoting; the
+                              Laplacians as (L + 11^T/N)^{-1}, their pseudo-inverse on the
+                              mean-free right-hand sides), exact to rounding; costs
+                              npad^2 + nf^2 + nv^2 doubles of device memory. */
 } mot_options;
 
 enum { MOT_MIX_HIST32 = 1, MOT_MIX_LF32 = 2, MOT_MIX_Q032 = 4, MOT_MIX_REFINE = 8, MOT_MIX_PRECOND = 16,

@@ -360,6 +360,23 @@ int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const 
     return it;
 }
 
+// Direct solve of a graph-Laplacian system L z = f (N rows, C columns), the
+// consistent one: the column mean of f is removed (and the column scaled by a
+// power of two, undone at the end), then z = Linv r with Linv the dense FP64
+// (L + 11^T/N)^{-1} (npd x npd, identity on the padding), which on mean-free
+// right-hand sides is the pseudo-inverse (minimum-norm solution).
+// r, z: npd x C doubles each; sc: C doubles.
+void direct_laplacian_solve(mot_handle* h, int N, int npd, const double* Linv, const double* f, int C, double* r,
+                            double* z, double* sc, cudaStream_t s) {
+    cudaMemsetAsync(r, 0, sizeof(double) * (size_t)npd * C, s);  // padded rows: zero
+    k_demean_cols<<<C, 256, 0, s>>>(N, C, f, r, sc);
+    h->launches++;
+    launch_gemm_rect(h, npd, npd, Linv, r, C, z, s);
+    const size_t blk = (size_t)N * C;
+    k_scale_cols<<<(int)std::min<size_t>(4096, (blk + 255) / 256), 256, 0, s>>>(N, C, sc, z);
+    h->launches++;
+}
+
 void dense_pad_identity(mot_handle* h, int n, int ne, double* A, cudaStream_t s) {
     if (2 * ne >= n) return;
     k_pad_identity<<<(n - 2 * ne + 255) / 256, 256, 0, s>>>(n, ne, A);

@@ -78,6 +78,8 @@ void dense_lap_plus_j(mot_handle* h, const DCsr& L, int npd, double* A, cudaStre
 int pcg_dense_prec(mot_handle* h, const DCsr& L, int npd, const float* M, const double* f, int C, double* z,
                    double* work, double* d_scal, float* fstage, double tol, int maxit, cudaStream_t s);
 void dense_inverse_from_lu(mot_handle* h, int n, const double* LU, const int* piv, double* X, cudaStream_t s);
+void direct_laplacian_solve(mot_handle* h, int N, int npd, const double* Linv, const double* f, int C, double* r,
+                            double* z, double* sc, cudaStream_t s);
 
 // extra launch wrappers (k_linalg.cu)
 void launch_pack2(mot_handle* h, const double* a, const double* b, int C, double* out, cudaStream_t s);
@@ -245,6 +247,11 @@ size_t work_doubles(mot_handle* h) {
 void project_sigma(mot_handle* h, const Work& W, const double* x, double* out, cudaStream_t s) {
     const int C = 2 * h->B;
     launch_sigma_t(h, x, C, W.fvec, s);
+    if (h->d_Lfinv64) {  // FP64 path with fp64_direct: the dense pseudo-inverse
+        direct_laplacian_solve(h, h->nf, h->dfpd, h->d_Lfinv64, W.fvec, C, h->d_dir_r, h->d_dir_z, h->d_dir_sc, s);
+        launch_sigma(h, h->d_dir_z, C, out, s);
+        return;
+    }
     if (h->d_Lfinvf && h->d_pcg_work && !h->precomputing)
         h->last_pcg_iters = pcg_dense_prec(h, h->Lf, h->nfpd, h->d_Lfinvf, W.fvec, C, W.zvec, h->d_pcg_work,
                                            h->d_pcg_scal, h->d_pcg_f32, h->opt.cg_tol, 50, s);
@@ -256,6 +263,11 @@ void project_sigma(mot_handle* h, const Work& W, const double* x, double* out, c
 // out = P^Lambda x for C columns
 void project_lambda(mot_handle* h, const Work& W, const double* x, int C, double* out, cudaStream_t s) {
     launch_lambda_t(h, x, C, W.fvec, s);
+    if (h->d_Lvinv64) {  // FP64 path with fp64_direct: the dense pseudo-inverse
+        direct_laplacian_solve(h, h->nv, h->dvpd, h->d_Lvinv64, W.fvec, C, h->d_dir_r, h->d_dir_z, h->d_dir_sc, s);
+        launch_lambda(h, h->d_dir_z, C, out, s);
+        return;
+    }
     launch_cg(h, h->Lv, nullptr, W.fvec, C, W.zvec, W.cgw, s);
     launch_lambda(h, W.zvec, C, out, s);
 }
@@ -267,8 +279,12 @@ void left_factor(mot_handle* h, const Work& W, const double* y1, const double* y
     project_sigma(h, W, y2, W.tmp, s);
     launch_axpby(h, n, 1.0, y2, -1.0, W.tmp, W.z2, s);  // z2 = P^{LH} y2
     launch_pack2(h, y1, W.z2, C, W.Y4, s);
-    launch_spmv(h, h->Gt, W.Y4, 2 * C, W.GY4, s);        // G^T Y
-    launch_cg(h, h->G, &h->Gt, W.GY4, 2 * C, W.X4, W.cgw, s);  // (G^T G) X = G^T Y
+    if (h->d_Ginv64) {  // FP64 path with fp64_direct: X = G^{-1} Y with the dense inverse
+        launch_gemm_rect(h, h->npad, h->npad, h->d_Ginv64, W.Y4, 2 * C, W.X4, s);
+    } else {
+        launch_spmv(h, h->Gt, W.Y4, 2 * C, W.GY4, s);        // G^T Y
+        launch_cg(h, h->G, &h->Gt, W.GY4, 2 * C, W.X4, W.cgw, s);  // (G^T G) X = G^T Y
+    }
     project_lambda(h, W, W.X4, 2 * C, W.PX4, s);
     launch_unpack_q(h, W.X4, W.PX4, C, W.q1, W.q2, s);  // q1 = P^{SH} x1, q2 = P^L x2
     launch_gemm(h, h->d_T0s, W.q1, C, W.t1, s);
@@ -742,6 +758,7 @@ MOT_API int mot_create(const mot_mesh* mesh, double eps_r, double mu_r, double d
         h->opt.refine_sweeps = opt->refine_sweeps;
         h->opt.fp64_precond = opt->fp64_precond;
         h->opt.hist_stall_test = opt->hist_stall_test;
+        h->opt.fp64_direct = opt->fp64_direct;
     }
     auto bad = [&](const char* m) {
         h->err = m;
@@ -1477,6 +1494,67 @@ int precompute_fp64_precond(mot_handle* h) {
     return MOT_OK;
 }
 
+// FP64 path with fp64_direct: dense FP64 inverses of the Gram matrix and of
+// the two graph Laplacians (plus 11^T/N), formed once by LU with partial
+// pivoting, so the left factor and the projectors are exact to rounding
+// instead of to the CG tolerance. tg: the Gram matrix's triplets in the
+// internal order.
+int prepare_fp64_direct(mot_handle* h, const std::vector<std::tuple<int, int, double>>& tg) {
+    cudaStream_t s = 0;
+    const int np = h->npad;
+    {  // G^{-1}: the leading npad x npad block of the inverse of [[G, 0], [0, I]] (a multiple of 64)
+        const int gpd = (np + 63) / 64 * 64;
+        std::vector<double> g((size_t)gpd * gpd, 0.0);
+        for (const auto& t : tg) g[(size_t)std::get<0>(t) * gpd + std::get<1>(t)] += std::get<2>(t);
+        for (int i = h->ne; i < gpd; i++) g[(size_t)i * gpd + i] = 1.0;
+        double* A = (double*)dalloc(h, sizeof(double) * (size_t)gpd * gpd);
+        double* inv = (double*)dalloc(h, sizeof(double) * (size_t)gpd * gpd);
+        int* piv = (int*)dalloc(h, sizeof(int) * (size_t)(gpd + 1));
+        h->d_Ginv64 = (double*)dalloc(h, sizeof(double) * (size_t)np * np);
+        if (!A || !inv || !piv || !h->d_Ginv64) return fail(h, MOT_EOOM, "device allocation (dense G inverse)");
+        CK(cudaMemcpy(A, g.data(), sizeof(double) * g.size(), cudaMemcpyHostToDevice));
+        const int bad = dense_lu(h, gpd, A, piv, piv + gpd, s);
+        if (bad == 0) {
+            dense_inverse_from_lu(h, gpd, A, piv, inv, s);
+            CK(cudaMemcpy2DAsync(h->d_Ginv64, sizeof(double) * np, inv, sizeof(double) * gpd, sizeof(double) * np, np,
+                                 cudaMemcpyDeviceToDevice, s));
+        }
+        CK(cudaDeviceSynchronize());
+        cudaFree(A);
+        cudaFree(inv);
+        cudaFree(piv);
+        h->device_bytes -= (int64_t)(2 * sizeof(double) * (size_t)gpd * gpd + sizeof(int) * (size_t)(gpd + 1));
+        if (bad != 0) return fail(h, MOT_EINVAL, "G is singular to working precision (LU pivot breakdown)");
+    }
+    auto lap = [&](const DCsr& L, int n, double** out, int* npd_out) -> int {
+        const int npd = (n + 63) / 64 * 64;
+        double* A = (double*)dalloc(h, sizeof(double) * (size_t)npd * npd);
+        int* piv = (int*)dalloc(h, sizeof(int) * (size_t)(npd + 1));
+        *out = (double*)dalloc(h, sizeof(double) * (size_t)npd * npd);
+        if (!A || !piv || !*out) return fail(h, MOT_EOOM, "device allocation (dense Laplacian inverse)");
+        dense_lap_plus_j(h, L, npd, A, s);
+        const int bad = dense_lu(h, npd, A, piv, piv + npd, s);
+        if (bad == 0) dense_inverse_from_lu(h, npd, A, piv, *out, s);
+        CK(cudaDeviceSynchronize());
+        cudaFree(A);
+        cudaFree(piv);
+        h->device_bytes -= (int64_t)(sizeof(double) * (size_t)npd * npd + sizeof(int) * (size_t)(npd + 1));
+        if (bad != 0) return fail(h, MOT_EINVAL, "a graph Laplacian plus 11^T/N is singular (surface not connected?)");
+        *npd_out = npd;
+        return MOT_OK;
+    };
+    int st;
+    if ((st = lap(h->Lf, h->nf, &h->d_Lfinv64, &h->dfpd)) != MOT_OK) return st;
+    if ((st = lap(h->Lv, h->nv, &h->d_Lvinv64, &h->dvpd)) != MOT_OK) return st;
+    const size_t cmax = 4 * MOT_MAX_B;  // widest block projected: the left factor's 4B columns
+    const size_t rows = (size_t)std::max(h->dfpd, h->dvpd);
+    h->d_dir_r = (double*)dalloc(h, sizeof(double) * rows * cmax);
+    h->d_dir_z = (double*)dalloc(h, sizeof(double) * rows * cmax);
+    h->d_dir_sc = (double*)dalloc(h, sizeof(double) * cmax);
+    if (!h->d_dir_r || !h->d_dir_z || !h->d_dir_sc) return fail(h, MOT_EOOM, "device allocation (direct solves)");
+    return MOT_OK;
+}
+
 }  // namespace
 
 MOT_API int mot_load_operators(mot_handle* h, const mot_operators* ops) {
@@ -1518,6 +1596,8 @@ MOT_API int mot_load_operators(mot_handle* h, const mot_operators* ops) {
     HostCsr G = csr_from_triplets(ne, ne, tg), Gt = csr_from_triplets(ne, ne, tgt);
     if ((st = upload_csr(h, G, h->G)) != MOT_OK) return st;
     if ((st = upload_csr(h, Gt, h->Gt)) != MOT_OK) return st;
+    if (h->opt.precision == MOT_PREC_FP64 && h->opt.fp64_direct && (st = prepare_fp64_direct(h, tg)) != MOT_OK)
+        return st;
     // RHS quadrature table
     h->nq = ops->nq;
     std::vector<double> x((size_t)np * h->nq * 3, 0.0), wf((size_t)np * h->nq * 3, 0.0);
@@ -2141,7 +2221,8 @@ MOT_API void mot_destroy(mot_handle* h) {
                     h->hist.tasks, h->hist.chunks, h->hist.chunk_ptr, h->lag0.tasks, h->lag0.chunks,
                     h->lag0.chunk_ptr, h->d_omega, h->d_colidx, h->d_tiles32, h->d_Q0, h->d_Q0f, h->d_LF,
                     h->d_LFf, h->d_Minvf, h->d_Minv64, h->d_Lfinvf, h->hist_tc_list.packed, h->hist_tc_list.chunks,
-                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16, h->d_sgws, h->d_emuws};
+                    h->hist_tc_list.rb_ptr, h->hist_tc_list.rb_chunks, h->d_tiles16, h->d_sgws, h->d_emuws,
+                    h->d_Ginv64, h->d_Lfinv64, h->d_Lvinv64, h->d_dir_r, h->d_dir_z, h->d_dir_sc};
     emu_free(h, &h->emu_Q0);
     emu_free(h, &h->emu_LF);
     emu_free(h, &h->emu_Q0s);

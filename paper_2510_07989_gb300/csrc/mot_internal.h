@@ -174,6 +174,14 @@ struct mot_handle {
     int tc_cap = 0;                // tasks per chunk the tensor-core list was cut with
     int tc_epi = 4;                // epilogue warps of the tensor-core history (4 or 8)
     int tc_tps = 1;                // tasks per pipeline stage of the tensor-core history (1 or 2)
+    // FP64 path with fp64_direct: dense inverses formed at load, in place of CG
+    double* d_Ginv64 = nullptr;    // G^{-1}, npad x npad
+    double* d_Lfinv64 = nullptr;   // (L_f + 11^T/N_f)^{-1}, dfpd x dfpd (identity on the padding)
+    double* d_Lvinv64 = nullptr;   // (L_v + 11^T/N_v)^{-1}, dvpd x dvpd
+    int dfpd = 0, dvpd = 0;
+    double* d_dir_r = nullptr;     // direct Laplacian solves: right-hand side and solution,
+    double* d_dir_z = nullptr;     // max(dfpd, dvpd) x 4 MOT_MAX_B each, and column scales
+    double* d_dir_sc = nullptr;
     double tc_lag_frac = 0;        // fraction of L2 a lag range of the list may fill
     bool tc_tuned = false;         // the three were chosen by mot_tune
     float tc_tune_ms = 0;          // the chosen configuration's launch time in the tuning (ms)

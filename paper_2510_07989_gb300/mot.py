@@ -37,7 +37,8 @@ class mot_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("device", ctypes.c_int32), ("gmres_tol", ctypes.c_double),
                 ("gmres_maxit", ctypes.c_int32), ("cg_tol", ctypes.c_double), ("cg_maxit", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("mixed_flags", ctypes.c_int32), ("refine_sweeps", ctypes.c_int32),
-                ("fp64_precond", ctypes.c_int32), ("hist_stall_test", ctypes.c_int32)]
+                ("fp64_precond", ctypes.c_int32), ("hist_stall_test", ctypes.c_int32),
+                ("fp64_direct", ctypes.c_int32)]
 
 
 class mot_lagmat(ctypes.Structure):
@@ -182,14 +183,14 @@ class Handle:
 
 def mot_create(verts, tris, eps_r, mu_r, dt, K, precision=MOT_PREC_FP64, device=0, gmres_tol=0.0,
                gmres_maxit=200, cg_tol=1e-14, cg_maxit=5000, timing=0, mixed_flags=0, refine_sweeps=0,
-               fp64_precond=0, hist_stall_test=0) -> Handle:
+               fp64_precond=0, hist_stall_test=0, fp64_direct=0) -> Handle:
     """gmres_tol <= 0 selects the library default (1e-13 FP64, 1e-11 mixed)."""
     lib = load_library()
     V = _c(verts, np.float64)
     Tr = _c(tris, np.int32)
     mesh = mot_mesh(V.shape[0], V.ctypes.data, Tr.shape[0], Tr.ctypes.data)
     opt = mot_options(precision, device, gmres_tol, gmres_maxit, cg_tol, cg_maxit, int(timing), int(mixed_flags),
-                      int(refine_sweeps), int(fp64_precond), int(hist_stall_test))
+                      int(refine_sweeps), int(fp64_precond), int(hist_stall_test), int(fp64_direct))
     out = ctypes.c_void_p()
     code = lib.mot_create(ctypes.byref(mesh), float(eps_r), float(mu_r), float(dt), int(K), ctypes.byref(opt),
                           ctypes.byref(out))

@@ -398,3 +398,34 @@ def test_star_pyramid_late_time_stability():
     assert np.abs(ev).max() < 0.95
     assert np.abs(ev - 1).min() > 0.1
 
+
+def test_extended_precision_oracle_matches_the_oracle(pr1_ops, pr1_system):
+    """oracle.extended evaluates the same definition in long double; where the
+    FP64 oracle is accurate (PR1, 200 steps through the pulse) the two agree
+    to FP64 rounding."""
+    from oracle import extended as X
+    exc = MS.single_wave(pr1_ops.dt, 30, 60)
+    n = 200
+    ref = O.march(pr1_system, exc, n)
+    W = X.ExtendedSystem(pr1_ops).march(exc, n).astype(np.float64)
+    assert np.abs(W - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_star_pyramid80_reference_is_reproduced():
+    """The stored extended-precision march of the 80-triangle pyramid
+    (tests/golden/star_pyramid80_extended.txt) is what its generator computes
+    from the seeded inputs with oracle.extended (to 1e-13 of the peak)."""
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(here, "make_star_pyramid80.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    _, W = mk.compute()
+    rows = [ln.split() for ln in open(os.path.join(here, "star_pyramid80_extended.txt")) if ln[:1] in ("p", "w")]
+    peak = float(rows[0][1])
+    assert abs(float(np.abs(W).max()) - peak) < 1e-13 * peak
+    vals = [(int(i), int(j), float(v)) for _, i, j, v in rows[1:]]
+    assert len(vals) == len(mk.STEPS) * len(mk.UNKNOWNS)
+    assert max(abs(float(W[i - 1, j]) - v) for i, j, v in vals) < 1e-13 * peak
+
