@@ -51,13 +51,19 @@
 // row block's column order, by 16-byte cp.async copies that place every
 // 16-byte piece straight into the swizzled MN-major A layout, each copying
 // thread arriving on the same FULL barrier once its copies have landed.
+// A pipeline stage holds the operands of TP = 1 or 2 tasks behind one FULL /
+// EMPTY barrier pair: the producers wait and arrive once per stage, the MMA
+// thread waits once and commits once per stage, so two tasks per stage halve
+// the barrier hand-offs (NS stages: 4 or 5 of one task, 2 or 3 of two).
 //
-// Warp roles (224 threads, one CTA per SM):
+// Warp roles (224 threads with four epilogue warps, 352 with eight; one CTA
+// per SM):
 //   warps 0-1  gather: coefficient rows by cp.async (each lane's arrival fires
 //              on completion of its copies, so the warps never wait for them)
 //              and the tile copies
 //   warp  2    TMEM allocation; lane 0 issues the MMAs
-//   warps 3-6  epilogue (TMEM -> registers, compensated sums, partial results)
+//   warps 3-6  epilogue (TMEM -> registers, compensated sums on packed FP32
+//   (or 3-10)  pairs, partial results)
 // Arrivals on a barrier are shared-memory atomics on one word: the epilogue
 // warps arrive once per warp, after a warp-level sync.
 // Every mbarrier wait is bounded in time; a wait that runs out raises the
