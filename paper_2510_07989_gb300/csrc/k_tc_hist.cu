@@ -790,8 +790,9 @@ TcJob job_of(mot_handle* h, long long step_i) {
 }
 
 // One launch of the history kernel over jobs[0 .. njobs) (all of one form);
-// the pipeline depth is the handles' tuned one (all equal), else the deepest
-// that fits.
+// the pipeline (stages x tasks per stage) is the first handle's tuned or set
+// one when it fits in shared memory, else the deepest one-task pipeline that
+// fits.
 void launch_jobs(mot_handle* h0, TcJobs& jobs, int nctas, int max_npad, int cap, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     once_per_device(attr, h0->dev, [] {

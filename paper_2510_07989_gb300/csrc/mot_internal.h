@@ -170,7 +170,7 @@ struct mot_handle {
                                    // (bulk form: [npad x 128] per slice, in swizzled 32-row blocks)
     uint16_t* d_win16 = nullptr;   // tensor-core path: bf16 slices of the windowed sums, [a][3 slices][npad][2B]
     bool tc_bulk = false;          // tensor-core history in the bulk form (global column order, blocked ring)
-    int tc_stages = 0;             // pipeline depth of the tensor-core history (0: the deepest that fits)
+    int tc_stages = 0;             // pipeline stages of the tensor-core history (0: the deepest that fits)
     int tc_cap = 0;                // tasks per chunk the tensor-core list was cut with
     int tc_epi = 4;                // epilogue warps of the tensor-core history (4 or 8)
     int tc_tps = 1;                // tasks per pipeline stage of the tensor-core history (1 or 2)
