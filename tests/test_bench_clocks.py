@@ -58,3 +58,27 @@ def test_sampler_process_end_to_end(tmp_path, monkeypatch):
     rec = c.stop()
     assert rec["in_region_only"] and 4 <= rec["samples"] <= 8
     assert rec["sm_mhz"] == 2070 and rec["reasons"] == [] and abs(rec["region_s"] - 1.0) < 0.2
+
+
+def test_reference_arm_line_on_the_host():
+    """`bench.py --impl reference` (the oracle on the host's cores, the
+    driver's reference arm) prints one JSON line with the contract's keys:
+    the metric of the default workload, impl, cpu_baseline, an e2e without
+    host-device copies; small workload, one step."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "torus32x12", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=900, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "torus32x12" and d["n_gpus"] == 1 and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["metric"] and d["unit"]
