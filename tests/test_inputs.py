@@ -331,3 +331,14 @@ def test_uneven_batch_recipe():
     other = MS.uneven_batch(24, seed=1)
     assert any(not np.array_equal(m.verts, m2.verts) for (m, _), (m2, _) in zip(b[3:], other[3:]) if m.nv == m2.nv) \
         or [m.nv for m, _ in b] != [m.nv for m, _ in other]
+
+
+def test_widening_inputs_reject_bad_parameters():
+    """The star pyramid needs n >= 3 tips, m >= 1, 0 < r_inner < r_tip and a
+    positive height; the Yukawa decay must be >= 0 (kappa = 0 is T_0)."""
+    from paper_2510_07989_gb300.inputs.assemble import assemble
+    for kw in (dict(n_points=2), dict(m=0), dict(r_inner=1.0), dict(r_inner=0.0), dict(height=0.0)):
+        with pytest.raises(ValueError):
+            MS.star_pyramid(**kw)
+    with pytest.raises(ValueError):
+        assemble(MS.icosphere(1), 2.0, 1.0, 0.2, kappa=-1.0)
