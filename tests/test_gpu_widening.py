@@ -67,8 +67,8 @@ def _extended_reference():
     the 80-triangle pyramid's march evaluated by the oracle in extended
     precision. On this mesh the march magnifies operator-level rounding, and
     FP64 evaluations of the oracle differ between machines' linear algebra by
-    up to ~2e-7 of the peak (the FP64 oracle on the GPU machine's host cores
-    does), so this is the reference."""
+    up to ~2e-7 of the peak (an aarch64 host's FP64 oracle does), so this
+    is the reference."""
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "star_pyramid80_extended.txt")
     rows = [ln.split() for ln in open(path) if ln[:1] in ("p", "w")]
     return float(rows[0][1]), [(int(i), int(j), float(v)) for _, i, j, v in rows[1:]]
