@@ -296,3 +296,24 @@ def companion(sys_: DenseSystem) -> np.ndarray:
     for k in range(1, K):
         C[k * n:(k + 1) * n, (k - 1) * n:k * n] = np.eye(n)
     return C
+
+
+def companion_top_eigenvalues(sys_: DenseSystem, k: int = 2, ncv: int = 300, tol: float = 1e-6) -> np.ndarray:
+    """The k eigenvalues of largest magnitude of the same companion matrix
+    (Section VI-A companion analysis) by Arnoldi on the operator applied
+    without forming it: (x_1 .. x_K) -> (-sum_k Q_0^{-1} Q_k x_k, x_1 .. x_{K-1}),
+    for meshes whose companion matrix is too large to decompose densely."""
+    from scipy.sparse.linalg import LinearOperator, eigs
+    Q = sys_.Q
+    K = len(Q) - 1
+    n = Q[0].shape[0]
+    top = -sla.lu_solve(sys_.lu, np.concatenate(Q[1:], axis=1))  # first block row, n x K n
+
+    def mv(x):
+        y = np.empty_like(x)
+        y[:n] = top @ x
+        y[n:] = x[:-n]
+        return y
+
+    op = LinearOperator((K * n, K * n), matvec=mv, dtype=np.float64)
+    return eigs(op, k=k, ncv=min(ncv, K * n - 1), which="LM", return_eigenvectors=False, tol=tol, maxiter=20000)

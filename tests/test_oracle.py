@@ -429,3 +429,29 @@ def test_star_pyramid80_reference_is_reproduced():
     assert len(vals) == len(mk.STEPS) * len(mk.UNKNOWNS)
     assert max(abs(float(W[i - 1, j]) - v) for i, j, v in vals) < 1e-13 * peak
 
+
+def test_companion_arnoldi_matches_the_dense_spectrum():
+    """The matrix-free Arnoldi evaluation of the companion spectrum (for
+    meshes too large for a dense eigendecomposition) gives the dense
+    spectral radius (PR1 mesh at c dt = 0.5)."""
+    ops = assemble(MS.icosphere(1), 2.0, 1.0, 0.5)
+    S = O.build_system(ops)
+    dense = np.abs(np.linalg.eigvals(O.companion(S))).max()
+    top = np.abs(O.companion_top_eigenvalues(S, k=2, tol=1e-10)).max()
+    assert abs(top - dense) < 1e-8 * dense
+
+
+def test_torus_companion_spectrum_inside_unit_circle():
+    """Section VI-A, second example: the multiply-connected torus is stable
+    under the qHP formulation. Torus 10 x 5 (genus 1: two global loops in
+    the loop space), eps_r = 4, c dt = 0.1 (k_max = 52, companion dimension
+    53 x 300): the largest eigenvalues stay strictly inside the unit circle
+    (radius ~0.987) and away from 1 + 0i, so no eigenvalue lies within
+    1 - radius of 1."""
+    ops = assemble(MS.torus(1.0, 0.3, 10, 5), 4.0, 1.0, 0.1)
+    assert ops.kmax == 52
+    top = O.companion_top_eigenvalues(O.build_system(ops), k=2)
+    radius = np.abs(top).max()
+    assert radius < 0.995
+    assert np.abs(top - 1).min() > 0.1
+
