@@ -43,3 +43,22 @@ def test_two_rank_reduction_and_distinct_batches():
     assert v0 == v1 == [11.0, 100.0]            # max over ranks of both timings
     assert thr0 == thr1 == pytest.approx(2 * 4 * 10 / 0.011)
     assert not np.allclose(p0, p1)               # each rank has its own plane waves
+
+
+def test_reference_arm_under_torchrun_two_ranks():
+    """The driver's N > 1 reference invocation: under torchrun with two ranks
+    only rank 0 runs the oracle and prints; the other rank exits 0 without
+    work, so the job prints exactly one JSON line (small torus, one step)."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), os.path.join(root, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--workload", "torus32x12", "--steps", "1", "--warmup", "0"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=900, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0
